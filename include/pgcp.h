@@ -1,0 +1,204 @@
+/*
+ * pgcp.h -- C ABI of the GB300 PGCP library (parallelizable global conformal
+ * parameterization of simply-connected surfaces via partial welding,
+ * Choi, Leung-Liu, Gu, Lui; arXiv 1903.12359).
+ *
+ * The problem statement is Section 4 / Algorithm 3 of the paper: given a
+ * triangle mesh (V, F) of a simply-connected surface and a set of cut edges,
+ * return planar (free boundary), unit-disk or unit-sphere coordinates of every
+ * vertex.
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; nothing traps or aborts.  After an error,
+ *    pgcp_last_error(ctx) holds a one-line message.
+ *  - Unless an argument says otherwise, pointers are DEVICE pointers owned by
+ *    the caller, and every call is ordered on the context's CUDA stream.
+ *    Calls that copy results to the host synchronise that stream.
+ *  - Index arrays are 0-based int32; coordinates are float64.
+ *  - V is [nv][3] row-major (x, y, z); F is [nf][3] row-major with faces
+ *    oriented consistently (counter-clockwise seen from the outside).
+ *  - Opaque handles are released with the matching *_free / *_destroy.
+ *  - A context is bound to the device current at pgcp_create and to one
+ *    stream; it is not thread-safe.
+ */
+#ifndef PGCP_H
+#define PGCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGCP_OK = 0,
+    PGCP_E_ARG = 1,           /* bad argument: sizes, indices, orientation, unknown cut edge */
+    PGCP_E_CUDA = 2,          /* a CUDA runtime call failed */
+    PGCP_E_OOM = 3,           /* device or host allocation failed */
+    PGCP_E_NONMANIFOLD = 4,   /* an edge is shared by more than two faces */
+    PGCP_E_TOPOLOGY = 5,      /* a piece is not a topological disk (pinch, hole, no boundary) */
+    PGCP_E_SCHEDULE = 6,      /* no valid welding order (shared arc not one run of >= 2 edges) */
+    PGCP_E_DEGENERATE = 7,    /* zero-area face */
+    PGCP_E_NO_CONVERGENCE = 8,/* an iterative solve hit its iteration limit above tolerance */
+    PGCP_E_NUMERIC = 9        /* NaN/Inf, or a welding step out of its domain */
+} pgcp_status;
+
+typedef enum { PGCP_FREE = 0, PGCP_DISK = 1, PGCP_SPHERE = 2 } pgcp_variant;
+typedef enum { PGCP_FP64 = 0, PGCP_FP32_REFINED = 1 } pgcp_precision;
+typedef enum { PGCP_WARM_COLD = 0, PGCP_WARM_WELDMAP = 1, PGCP_WARM_LEARNED = 2 } pgcp_warm_start;
+
+typedef struct {
+    int32_t variant;          /* pgcp_variant */
+    int32_t precision;        /* pgcp_precision: PCG arithmetic of both solve stages */
+    double  tol;              /* relative residual ||b - A x|| / ||b|| per piece and coordinate */
+    int32_t max_iters;        /* PCG iterations per solve (inner solves for FP32_REFINED) */
+    int32_t max_refine;       /* outer FP64 refinement steps (FP32_REFINED) */
+    double  inner_tol;        /* relative residual reduction of one inner FP32 solve */
+    int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve */
+    int32_t interior_map_fp64;/* 1: weld-map the interior in FP64 (else FP32) */
+    int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
+    int32_t reserved[7];
+} pgcp_options;
+
+/* Per-call statistics (host struct, filled by pgcp_global_solve). */
+typedef struct {
+    int32_t K;                 /* pieces */
+    int32_t n_welds;           /* partial (+ closed) welds performed */
+    int32_t dncp_iters;        /* PCG iterations of the local solve (max over refinement steps summed) */
+    int32_t final_iters;       /* PCG iterations of the final Laplace solve */
+    int32_t dncp_refine;       /* outer refinement steps, local solve */
+    int32_t final_refine;      /* outer refinement steps, final solve */
+    double  dncp_relres;       /* max over pieces and coordinates of the true FP64 relative residual */
+    double  final_relres;
+    double  seam_mismatch;     /* max |coords of a vertex in two pieces| after the final solve */
+    double  ms_partition, ms_assembly, ms_local, ms_weld, ms_final;  /* stage times (CUDA events) */
+    int64_t nnz;               /* stored entries of all piece Laplacians */
+    int64_t n_copies;          /* sum of piece vertex counts */
+} pgcp_stats;
+
+/* Angle-distortion statistics of a result (Section 5 definition, degrees). */
+typedef struct {
+    double mean, sd, median, iqr, max;   /* over |d| of all corners; sd with ddof = 0 */
+    int64_t n_corners;
+    int64_t flips;                        /* faces with signed area <= 0 (planar) or
+                                             negative orientation on the sphere */
+    double  max_mu;                       /* max |mu| of the piecewise-linear map (planar results) */
+} pgcp_distortion;
+
+typedef struct pgcp_ctx pgcp_ctx;    /* opaque; one per CUDA stream */
+typedef struct pgcp_part pgcp_part;  /* opaque; partition + all per-piece device state */
+
+/* Default options: DISK, FP32_REFINED, tol 1e-10, 20000 iterations, 8 refinement
+ * steps, inner_tol 1e-4, weld-map warm start, FP32 interior map. */
+void pgcp_default_options(pgcp_options* opt);
+
+/* Create a context on the current device.  cuda_stream: a cudaStream_t, or NULL
+ * for the legacy default stream.  opt may be NULL (defaults). */
+pgcp_status pgcp_create(pgcp_ctx** out, const pgcp_options* opt, void* cuda_stream);
+pgcp_status pgcp_destroy(pgcp_ctx* ctx);
+pgcp_status pgcp_set_options(pgcp_ctx* ctx, const pgcp_options* opt);
+const char* pgcp_last_error(const pgcp_ctx* ctx);
+const char* pgcp_status_string(pgcp_status s);
+
+/*
+ * Surface partition (Section 4.1).  Faces are joined across every edge that is
+ * neither a cut edge nor a boundary edge; each connected component is a piece.
+ * Pieces are labelled by the rank of their smallest face id; a piece's
+ * vertices are listed in ascending global id and its boundary loop runs
+ * counter-clockwise from its smallest global id.  Every piece must be a
+ * topological disk (else PGCP_E_TOPOLOGY); the welding order is fixed here
+ * (else PGCP_E_SCHEDULE).
+ *   V [nv*3], F [nf*3]: mesh.  cut_edges [n_cut*2]: undirected cut edges (may be
+ *   NULL with n_cut = 0); or face_labels [nf] (may be NULL): every edge between
+ *   faces of different labels is a cut edge (cut_edges is then ignored).
+ *   host_ptrs: 1 if V, F, cut_edges, face_labels are host pointers, 0 if device.
+ *   closed: 1 for a genus-0 closed surface (sphere variant: last weld closed).
+ * The part copies the mesh; the caller's buffers may be freed afterwards.
+ */
+pgcp_status pgcp_partition(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                           const int32_t* cut_edges, int64_t n_cut, const int32_t* face_labels,
+                           int32_t host_ptrs, int32_t closed, pgcp_part** out);
+
+/* Many independent meshes in one part (batched solves, one graph of launches).
+ * Each array holds per-mesh pointers; host_ptrs as above.  Pieces of mesh b
+ * follow those of mesh b-1. */
+pgcp_status pgcp_partition_batch(pgcp_ctx* ctx, int32_t n_mesh, const double* const* V, const int64_t* nv,
+                                 const int32_t* const* F, const int64_t* nf,
+                                 const int32_t* const* face_labels, int32_t host_ptrs, int32_t closed,
+                                 pgcp_part** out);
+
+pgcp_status pgcp_part_free(pgcp_part* part);
+
+/* Sizes of a part (host outputs; any pointer may be NULL). */
+pgcp_status pgcp_part_info(const pgcp_part* part, int32_t* K, int64_t* n_copies, int64_t* nnz,
+                           int64_t* n_loop, int32_t* n_welds, int32_t* n_mesh);
+
+/* Partition outputs (device outputs, caller-allocated; any may be NULL):
+ * face_label [nf_total], piece_voff [K+1] (int64), piece_verts [n_copies]
+ * (global vertex ids, ascending within each piece), loop_off [K+1] (int64),
+ * loop_verts [n_loop] (global ids, ccw, canonical start). */
+pgcp_status pgcp_part_get_partition(pgcp_ctx* ctx, const pgcp_part* part, int32_t* face_label,
+                                    int64_t* piece_voff, int32_t* piece_verts, int64_t* loop_off,
+                                    int32_t* loop_verts);
+
+/*
+ * Local conformal parameterization (Section 4.2): assembles every piece's
+ * cotangent Laplacian (positive semidefinite sign: L_pq = -(cot a + cot b)/2,
+ * L_pp = -sum_q L_pq) into one block-diagonal CSR, then solves DNCP
+ *   ((L (+) L) - M) [x; y] = 0,  M_{p,n+q} = M_{n+q,p} = 1/2, M_{q,n+p} = M_{n+p,q} = -1/2
+ * for every boundary edge p -> q, with loop position 0 pinned at (0, 0) and
+ * position floor(b/2) at (1, 0), by batched PCG; then translates each piece so
+ * its reference vertex (first interior vertex at or after local index
+ * floor(n/2)) is at 0.
+ */
+pgcp_status pgcp_local_param(pgcp_ctx* ctx, pgcp_part* part);
+
+/* CSR of the assembled Laplacians (device outputs, caller-allocated; any may be
+ * NULL): row_ptr [n_copies+1] (int64), col [nnz] (piece-local column ids,
+ * ascending, diagonal stored), val [nnz] (float64). */
+pgcp_status pgcp_part_get_csr(pgcp_ctx* ctx, const pgcp_part* part, int64_t* row_ptr, int32_t* col,
+                              double* val);
+
+/* Current complex coordinates of every piece vertex copy (device output
+ * [n_copies*2], (re, im) pairs, piece-major, ascending global id within a
+ * piece).  which: 0 = DNCP result (local frame), 1 = welded (boundary copies
+ * FP64; interior copies hold the interior weld map), 2 = final solve. */
+pgcp_status pgcp_part_get_coords(pgcp_ctx* ctx, const pgcp_part* part, int32_t which, double* out);
+
+/*
+ * Partial welding (Algorithms 1 and 2) of the pieces in the fixed order, then
+ * the disk constraint (geodesic algorithm on the global boundary onto the unit
+ * disk) or, for a closed surface, the closed weld of the last piece.  FP64 on
+ * the boundary; the interior is mapped too (FP32 by default) as the warm start
+ * of the final solve.
+ */
+pgcp_status pgcp_weld(pgcp_ctx* ctx, pgcp_part* part);
+
+/*
+ * Final harmonic solve (Section 4.5): Laplace equation on every piece with the
+ * welded boundary, batched PCG; gather (each vertex takes the copy of the
+ * lowest-label piece holding it); stereographic projection for the sphere.
+ *   out: [nv_total*2] (free/disk) or [nv_total*3] (sphere), device unless
+ *   host_out = 1.  st: host struct, may be NULL.
+ */
+pgcp_status pgcp_global_solve(pgcp_ctx* ctx, pgcp_part* part, double* out, int32_t host_out, pgcp_stats* st);
+
+/* Angle distortion, flips and max |mu| of coordinates U (device, [nv*2] or
+ * [nv*3] per the part's variant) against the part's mesh.  met: host. */
+pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met);
+
+/*
+ * One-shot convenience: partition + local_param + weld + global_solve.
+ * variant selects the output (free: [nv*2], disk: [nv*2], sphere: [nv*3]).
+ * host_ptrs = 1: V, F, cut_edges and out are host pointers (the copies are
+ * part of the call).  st may be NULL.
+ */
+pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                     const int32_t* cut_edges, int64_t n_cut, const int32_t* face_labels,
+                     int32_t host_ptrs, double* out, pgcp_stats* st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGCP_H */

@@ -196,8 +196,12 @@ def stereo_from_inverted(w: np.ndarray) -> np.ndarray:
 
 
 def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
-         map_interior: bool = False) -> Result:
-    """Run Algorithm 3.  ``variant`` is "free", "disk" or "sphere"."""
+         map_interior: bool = False, local=None) -> Result:
+    """Run Algorithm 3.  ``variant`` is "free", "disk" or "sphere".
+
+    ``local`` (tests only): per-piece complex coordinates to use instead of the
+    DNCP solve, so the welding can be compared on identical inputs.
+    """
     V = np.asarray(V, dtype=np.float64)
     P = partition(V, F, cut_edges=cut_edges, face_labels=face_labels)
     welds = weld_schedule(P, closed_surface=(variant == "sphere"))
@@ -207,7 +211,10 @@ def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
         X = V[P.verts[i]]
         L = cotan_laplacian(X, P.local_F[i])
         ll = np.searchsorted(P.verts[i], P.loops[i])
-        u, ref = dncp(X, P.local_F[i], ll, L)
+        if local is None:
+            u, ref = dncp(X, P.local_F[i], ll, L)
+        else:
+            u, ref = np.asarray(local[i], dtype=np.complex128), -1
         res.L.append(L)
         res.local.append(u)
         res.ref.append(ref)

@@ -1,0 +1,280 @@
+"""Python binding of the PGCP CUDA library (argument marshalling only).
+
+Every computation runs in libpgcp.so (include/pgcp.h); this module converts
+torch tensors / numpy arrays into pointers and sizes, passes the current CUDA
+stream, and raises ``PgcpError`` on a non-zero status.  Importing it loads the
+library and raises if it is missing or was built for another machine.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpgcp.so")
+
+FREE, DISK, SPHERE = 0, 1, 2
+FP64, FP32_REFINED = 0, 1
+WARM_COLD, WARM_WELDMAP, WARM_LEARNED = 0, 1, 2
+
+STATUS = {0: "OK", 1: "ARG", 2: "CUDA", 3: "OOM", 4: "NONMANIFOLD", 5: "TOPOLOGY", 6: "SCHEDULE",
+          7: "DEGENERATE", 8: "NO_CONVERGENCE", 9: "NUMERIC"}
+
+
+class PgcpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+
+
+class Options(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double), ("max_iters", C.c_int32),
+                ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("warm_start", C.c_int32),
+                ("interior_map_fp64", C.c_int32), ("block_rows_log2", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("K", C.c_int32), ("n_welds", C.c_int32), ("dncp_iters", C.c_int32), ("final_iters", C.c_int32),
+                ("dncp_refine", C.c_int32), ("final_refine", C.c_int32), ("dncp_relres", C.c_double),
+                ("final_relres", C.c_double), ("seam_mismatch", C.c_double), ("ms_partition", C.c_double),
+                ("ms_assembly", C.c_double), ("ms_local", C.c_double), ("ms_weld", C.c_double),
+                ("ms_final", C.c_double), ("nnz", C.c_int64), ("n_copies", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Distortion(C.Structure):
+    _fields_ = [("mean", C.c_double), ("sd", C.c_double), ("median", C.c_double), ("iqr", C.c_double),
+                ("max", C.c_double), ("n_corners", C.c_int64), ("flips", C.c_int64), ("max_mu", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# exported symbols and their signatures (name -> (restype, argtypes))
+_P = C.c_void_p
+SIGNATURES = {
+    "pgcp_default_options": (None, [C.POINTER(Options)]),
+    "pgcp_create": (C.c_int, [C.POINTER(_P), C.POINTER(Options), _P]),
+    "pgcp_destroy": (C.c_int, [_P]),
+    "pgcp_set_options": (C.c_int, [_P, C.POINTER(Options)]),
+    "pgcp_last_error": (C.c_char_p, [_P]),
+    "pgcp_status_string": (C.c_char_p, [C.c_int]),
+    "pgcp_partition": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, C.c_int32,
+                                 C.POINTER(_P)]),
+    "pgcp_partition_batch": (C.c_int, [_P, C.c_int32, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(_P),
+                                       C.POINTER(C.c_int64), C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(_P)]),
+    "pgcp_part_free": (C.c_int, [_P]),
+    "pgcp_part_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pgcp_part_get_partition": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pgcp_local_param": (C.c_int, [_P, _P]),
+    "pgcp_part_get_csr": (C.c_int, [_P, _P, _P, _P, _P]),
+    "pgcp_part_get_coords": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "pgcp_weld": (C.c_int, [_P, _P]),
+    "pgcp_global_solve": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Stats)]),
+    "pgcp_metrics": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
+    "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
+                           C.POINTER(Stats)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpgcp.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_1903_12359_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().pgcp_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(C.c_void_p)
+
+
+def _dev(a, dtype):
+    """A contiguous CUDA tensor of dtype from a numpy array or tensor."""
+    if isinstance(a, torch.Tensor):
+        return a.to(device="cuda", dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+class Context:
+    """A library context bound to the current device and a CUDA stream."""
+
+    def __init__(self, options: Options | None = None, stream: torch.cuda.Stream | None = None, **kw):
+        lib = load()
+        self.options = options if options is not None else default_options(**kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = lib.pgcp_create(C.byref(h), C.byref(self.options), C.c_void_p(self.stream.cuda_stream))
+        if st:
+            raise PgcpError(st, "pgcp_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st:
+            raise PgcpError(st, load().pgcp_last_error(self.h).decode())
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        self.check(load().pgcp_set_options(self.h, C.byref(self.options)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pgcp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- stages
+    def partition(self, V, F, cut_edges=None, face_labels=None, closed=False) -> "Part":
+        Vd = _dev(V, torch.float64)
+        Fd = _dev(F, torch.int32)
+        cd = _dev(cut_edges, torch.int32) if cut_edges is not None and len(cut_edges) else None
+        ld = _dev(face_labels, torch.int32) if face_labels is not None else None
+        out = C.c_void_p()
+        self.check(load().pgcp_partition(self.h, _ptr(Vd), Vd.shape[0], _ptr(Fd), Fd.shape[0], _ptr(cd),
+                                         0 if cd is None else cd.shape[0], _ptr(ld), 0, int(closed), C.byref(out)))
+        return Part(self, out, nv=Vd.shape[0], nf=Fd.shape[0], closed=closed)
+
+    def partition_batch(self, meshes, closed=False) -> "Part":
+        """meshes: list of (V, F, face_labels)."""
+        Vs = [_dev(m[0], torch.float64) for m in meshes]
+        Fs = [_dev(m[1], torch.int32) for m in meshes]
+        Ls = [_dev(m[2], torch.int32) for m in meshes]
+        n = len(meshes)
+        arrV = (C.c_void_p * n)(*[t.data_ptr() for t in Vs])
+        arrF = (C.c_void_p * n)(*[t.data_ptr() for t in Fs])
+        arrL = (C.c_void_p * n)(*[t.data_ptr() for t in Ls])
+        nv = (C.c_int64 * n)(*[t.shape[0] for t in Vs])
+        nf = (C.c_int64 * n)(*[t.shape[0] for t in Fs])
+        out = C.c_void_p()
+        self.check(load().pgcp_partition_batch(self.h, n, arrV, nv, arrF, nf, arrL, 0, int(closed), C.byref(out)))
+        return Part(self, out, nv=sum(t.shape[0] for t in Vs), nf=sum(t.shape[0] for t in Fs), closed=closed,
+                    keep=(Vs, Fs, Ls))
+
+    def run(self, V, F, cut_edges=None, face_labels=None, host=True):
+        """One-shot pipeline.  host=True: numpy in, numpy out (copies inside the call)."""
+        dim = 3 if self.options.variant == SPHERE else 2
+        st = Stats()
+        if host:
+            Vh = np.ascontiguousarray(V, dtype=np.float64)
+            Fh = np.ascontiguousarray(F, dtype=np.int32)
+            ch = None if cut_edges is None else np.ascontiguousarray(cut_edges, dtype=np.int32)
+            lh = None if face_labels is None else np.ascontiguousarray(face_labels, dtype=np.int32)
+            out = np.empty((Vh.shape[0], dim), dtype=np.float64)
+            self.check(load().pgcp_run(self.h, _ptr(Vh), Vh.shape[0], _ptr(Fh), Fh.shape[0], _ptr(ch),
+                                       0 if ch is None else ch.shape[0], _ptr(lh), 1, _ptr(out), C.byref(st)))
+            return out, st.as_dict()
+        Vd, Fd = _dev(V, torch.float64), _dev(F, torch.int32)
+        cd = None if cut_edges is None else _dev(cut_edges, torch.int32)
+        ld = None if face_labels is None else _dev(face_labels, torch.int32)
+        out = torch.empty((Vd.shape[0], dim), dtype=torch.float64, device="cuda")
+        self.check(load().pgcp_run(self.h, _ptr(Vd), Vd.shape[0], _ptr(Fd), Fd.shape[0], _ptr(cd),
+                                   0 if cd is None else cd.shape[0], _ptr(ld), 0, _ptr(out), C.byref(st)))
+        return out, st.as_dict()
+
+
+class Part:
+    def __init__(self, ctx: Context, h, nv, nf, closed, keep=None):
+        self.ctx, self.h, self.nv, self.nf, self.closed = ctx, h, nv, nf, closed
+        self._keep = keep
+        self.stats = None
+
+    def info(self):
+        K, nc, nnz, nl, nw, nm = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        self.ctx.check(load().pgcp_part_info(self.h, C.byref(K), C.byref(nc), C.byref(nnz), C.byref(nl),
+                                             C.byref(nw), C.byref(nm)))
+        return {"K": K.value, "n_copies": nc.value, "nnz": nnz.value, "n_loop": nl.value, "n_welds": nw.value,
+                "n_mesh": nm.value}
+
+    def partition_arrays(self):
+        i = self.info()
+        d = "cuda"
+        fl = torch.empty(self.nf, dtype=torch.int32, device=d)
+        voff = torch.empty(i["K"] + 1, dtype=torch.int64, device=d)
+        verts = torch.empty(i["n_copies"], dtype=torch.int32, device=d)
+        loff = torch.empty(i["K"] + 1, dtype=torch.int64, device=d)
+        loops = torch.empty(i["n_loop"], dtype=torch.int32, device=d)
+        self.ctx.check(load().pgcp_part_get_partition(self.ctx.h, self.h, _ptr(fl), _ptr(voff), _ptr(verts),
+                                                      _ptr(loff), _ptr(loops)))
+        return fl, voff, verts, loff, loops
+
+    def local_param(self):
+        self.ctx.check(load().pgcp_local_param(self.ctx.h, self.h))
+
+    def csr(self):
+        i = self.info()
+        rp = torch.empty(i["n_copies"] + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(i["nnz"], dtype=torch.int32, device="cuda")
+        val = torch.empty(i["nnz"], dtype=torch.float64, device="cuda")
+        self.ctx.check(load().pgcp_part_get_csr(self.ctx.h, self.h, _ptr(rp), _ptr(col), _ptr(val)))
+        return rp, col, val
+
+    def coords(self, which: int):
+        """0: DNCP (local frame), 1: welded / weld map, 2: final; complex128 [n_copies]."""
+        i = self.info()
+        out = torch.empty((i["n_copies"], 2), dtype=torch.float64, device="cuda")
+        self.ctx.check(load().pgcp_part_get_coords(self.ctx.h, self.h, which, _ptr(out)))
+        return torch.complex(out[:, 0], out[:, 1])
+
+    def weld(self):
+        self.ctx.check(load().pgcp_weld(self.ctx.h, self.h))
+
+    def global_solve(self, out=None):
+        dim = 3 if self.closed else 2
+        if out is None:
+            out = torch.empty((self.nv, dim), dtype=torch.float64, device="cuda")
+        st = Stats()
+        self.ctx.check(load().pgcp_global_solve(self.ctx.h, self.h, _ptr(out), 0, C.byref(st)))
+        self.stats = st.as_dict()
+        return out
+
+    def metrics(self, U):
+        m = Distortion()
+        self.ctx.check(load().pgcp_metrics(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
+        return m.as_dict()
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().pgcp_part_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

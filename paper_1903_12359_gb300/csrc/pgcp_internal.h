@@ -1,0 +1,208 @@
+// Internal declarations of the PGCP CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pgcp.h"
+
+namespace pgcp {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+    pgcp_status code;
+    std::string msg;
+};
+
+// Thrown inside the library, turned into a status at the C ABI boundary.
+[[noreturn]] void fail(pgcp_status code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define PGCP_CUDA(call) ::pgcp::check_cuda((call), #call)
+
+// Device-side error flags (bit set by kernels, read back by the host).
+enum DevErr : uint32_t {
+    DE_NONMANIFOLD = 1u << 0,
+    DE_ORIENT = 1u << 1,
+    DE_CUT_MISSING = 1u << 2,
+    DE_DEGENERATE = 1u << 3,
+    DE_VALENCE = 1u << 4,
+    DE_NUMERIC = 1u << 5,
+    DE_UNION_LIMIT = 1u << 6,
+    DE_WELD_DOMAIN = 1u << 7,
+    DE_HASH_FULL = 1u << 8,
+};
+
+// ------------------------------------------------------------------ device memory
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on one stream).
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        if (count == 0) return;
+        cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            if (e == cudaErrorMemoryAllocation) fail(PGCP_E_OOM, "device allocation failed");
+            check_cuda(e, "cudaMallocAsync");
+        }
+    }
+    void zero() {
+        if (n) PGCP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+};
+
+// ------------------------------------------------------------------ welding records
+
+// One elementary map of a welding chain (layout shared by the phase-1 builder
+// and the phase-2 appliers).
+enum RecKind : int32_t { R_SQRT_RATIO = 0, R_OPEN = 1, R_MOB_POLE = 2, R_CLOSE = 3, R_POLE_SQ = 4, R_MOBIUS = 5 };
+
+struct __align__(16) Rec {
+    int32_t kind;
+    int32_t pad;
+    double branch;
+    double p[8];
+};
+
+// ------------------------------------------------------------------ part (device state)
+
+struct WeldPlan {             // one weld, host description (topology only)
+    int32_t mesh;
+    int32_t piece;            // S
+    int32_t k;                // shared edges
+    int32_t closed;           // closed weld (sphere)
+    int32_t first;            // first weld of its mesh (C is a single piece)
+    std::vector<int32_t> members;   // pieces of C before the weld
+    std::vector<int64_t> a_rows;    // copy rows of a_0..a_m (C side)
+    std::vector<int64_t> b_rows;    // copy rows of b_0..b_n (S side)
+    std::vector<int32_t> a_glob;
+    std::vector<int32_t> new_loop;  // global ids of C's loop after the weld (empty if closed)
+};
+
+struct MeshInfo {
+    int64_t v0, nv, f0, nf;   // offsets into the concatenated vertex / face arrays
+    int32_t piece0, npiece;   // pieces of this mesh: [piece0, piece0 + npiece)
+};
+
+struct Part {
+    // mesh (concatenated over the batch)
+    int64_t nv = 0, nf = 0;
+    int32_t closed = 0;
+    std::vector<MeshInfo> meshes;
+    DBuf<double> V;           // [nv*3]
+    DBuf<int32_t> F;          // [nf*3]
+    // partition
+    int32_t K = 0;
+    DBuf<int32_t> face_label; // [nf]
+    std::vector<int64_t> voff, foff;   // host copies [K+1]
+    DBuf<int64_t> d_voff;     // [K+1]
+    DBuf<int32_t> copy_vert;  // [Nc] global vertex of each copy (row)
+    DBuf<int32_t> row_piece;  // [Nc]
+    DBuf<int32_t> cF;         // [nf*3] faces in piece order, as copy rows
+    DBuf<int32_t> first_copy; // [nv] copy of the lowest-label piece holding v
+    int64_t Nc = 0;
+    // boundary loops
+    std::vector<int64_t> loff;         // [K+1]
+    std::vector<int64_t> loop_rows;    // copy rows, ccw
+    std::vector<int32_t> loop_glob;    // global ids
+    DBuf<int64_t> d_loff;
+    DBuf<int32_t> d_loop_rows;
+    DBuf<int32_t> d_loop_glob;
+    DBuf<int2> nb;            // [Nc] (prev, next) loop rows for boundary rows, (-1,-1) inside
+    DBuf<uint8_t> is_bnd;     // [Nc]
+    std::vector<int64_t> pin0, pin1, ref;   // per piece: copy rows
+    // schedule
+    std::vector<WeldPlan> welds;
+    // CSR (block diagonal over pieces; columns are global rows)
+    DBuf<int32_t> row_ptr;    // [Nc+1] (int32: nnz < 2^31)
+    DBuf<int32_t> col;
+    DBuf<double> val64;
+    DBuf<float> val32;
+    DBuf<double> diag64;
+    int64_t nnz = 0;
+    // coordinates
+    DBuf<double2> local;      // DNCP (local frame)
+    DBuf<double2> welded;     // FP64 welded coords (boundary rows exact; interior = weld map)
+    DBuf<double2> final;      // final solve
+    int32_t sphere_w_piece = -1;
+    int32_t have_local = 0, have_weld = 0, have_final = 0;
+    pgcp_stats stats{};
+};
+
+}  // namespace pgcp
+
+// ------------------------------------------------------------------ context
+
+struct pgcp_ctx {
+    pgcp_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+    pgcp::DBuf<uint32_t> err;        // device error flags
+};
+
+struct pgcp_part {
+    pgcp::Part p;
+};
+
+namespace pgcp {
+
+// ------------------------------------------------------------------ primitives (primitives.cu)
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+void radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s);
+uint32_t read_errors(pgcp_ctx* ctx);
+
+// ------------------------------------------------------------------ stages
+
+struct SolveResult {
+    int iters = 0;        // PCG iterations (summed over refinement steps)
+    int refine = 0;       // outer refinement steps
+    double relres = 0.0;  // max true FP64 relative residual over pieces and coordinates
+};
+// Batched PCG on all pieces; x holds fixed values and the initial guess.
+SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, double2* x);
+
+void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels_or_null, const int32_t* d_cut, int64_t n_cut);
+void build_schedule(pgcp_ctx* ctx, Part& P);
+void assemble_laplacian(pgcp_ctx* ctx, Part& P);
+void solve_dncp(pgcp_ctx* ctx, Part& P);
+void run_welds(pgcp_ctx* ctx, Part& P);
+void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out);
+void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace pgcp

@@ -1,0 +1,175 @@
+// Stage drivers around the batched PCG: DNCP set-up and local frame
+// (Section 4.2), final Laplace solve with the welded boundary (Section 4.5),
+// gather (lowest label wins) and stereographic projection (Algorithm 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pgcp_internal.h"
+
+namespace pgcp {
+
+namespace {
+
+__global__ void k_dncp_init(int64_t n, uint8_t* __restrict__ fixed, double2* __restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        fixed[i] = 0;
+        x[i] = make_double2(0.0, 0.0);
+    }
+}
+
+__global__ void k_dncp_pins(const int32_t* __restrict__ pin_rows, int32_t K, uint8_t* __restrict__ fixed,
+                            double2* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    int p0 = pin_rows[2 * i], p1 = pin_rows[2 * i + 1];
+    fixed[p0] = 1;
+    fixed[p1] = 1;
+    x[p0] = make_double2(0.0, 0.0);
+    x[p1] = make_double2(1.0, 0.0);
+}
+
+// translate each piece so its reference vertex is at 0
+__global__ void k_translate(int64_t n, const int32_t* __restrict__ row_piece, const int32_t* __restrict__ ref_rows,
+                            const double2* __restrict__ x, double2* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = ref_rows[row_piece[i]];
+    double2 v = x[i];
+    if (r >= 0) {
+        double2 c = x[r];
+        v.x = v.x - c.x;
+        v.y = v.y - c.y;
+    }
+    out[i] = v;
+}
+
+__global__ void k_final_init(int64_t n, const uint8_t* __restrict__ is_bnd, const double2* __restrict__ welded,
+                             int cold, double2* __restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = (is_bnd[i] || !cold) ? welded[i] : make_double2(0.0, 0.0);
+}
+
+// out[v] from the lowest-label copy; seam mismatch = max |copy - chosen copy|
+__global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, const int32_t* __restrict__ first_copy,
+                         const int32_t* __restrict__ row_piece, int32_t w_piece, const double2* __restrict__ X,
+                         int dim, double* __restrict__ out, unsigned long long* __restrict__ mism) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nc) return;
+    const int v = copy_vert[i];
+    const int f = first_copy[v];
+    double a[3], b[3];
+    auto coords = [&](int row, double* c) {
+        double2 z = X[row];
+        if (dim == 2) {
+            c[0] = z.x;
+            c[1] = z.y;
+            c[2] = 0.0;
+        } else {
+            // orientation-preserving inverse stereographic projection; the piece
+            // holding infinity is stored in the chart w = 1/z
+            double r2 = z.x * z.x + z.y * z.y, d = 1.0 + r2;
+            if (row_piece[row] == w_piece) {
+                c[0] = 2.0 * z.x / d;
+                c[1] = 2.0 * z.y / d;
+                c[2] = (1.0 - r2) / d;
+            } else {
+                c[0] = 2.0 * z.x / d;
+                c[1] = -2.0 * z.y / d;
+                c[2] = (r2 - 1.0) / d;
+            }
+        }
+    };
+    coords((int)i, a);
+    if (f == (int)i) {
+        for (int c = 0; c < dim; ++c) out[(int64_t)dim * v + c] = a[c];
+    } else {
+        coords(f, b);
+        double m = 0.0;
+        for (int c = 0; c < dim; ++c) m = fmax(m, fabs(a[c] - b[c]));
+        atomicMax(mism, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
+
+}  // namespace
+
+void solve_dncp(pgcp_ctx* ctx, Part& P) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P.Nc;
+    DBuf<uint8_t> fixed;
+    DBuf<double2> x;
+    DBuf<int32_t> pins, refs;
+    fixed.alloc(n, s);
+    x.alloc(n, s);
+    std::vector<int32_t> hp(2 * P.K), hr(P.K);
+    for (int i = 0; i < P.K; ++i) {
+        hp[2 * i] = (int32_t)P.pin0[i];
+        hp[2 * i + 1] = (int32_t)P.pin1[i];
+        hr[i] = (int32_t)P.ref[i];
+    }
+    pins.alloc(2 * P.K, s);
+    refs.alloc(P.K, s);
+    PGCP_CUDA(cudaMemcpyAsync(pins.p, hp.data(), hp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    PGCP_CUDA(cudaMemcpyAsync(refs.p, hr.data(), hr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_dncp_init<<<nblk(n), 256, 0, s>>>(n, fixed.p, x.p);
+    k_dncp_pins<<<nblk(P.K), 256, 0, s>>>(pins.p, P.K, fixed.p, x.p);
+    PGCP_CUDA(cudaGetLastError());
+    SolveResult r = pcg_solve(ctx, P, 1, fixed.p, x.p);
+    P.stats.dncp_iters = r.iters;
+    P.stats.dncp_refine = r.refine;
+    P.stats.dncp_relres = r.relres;
+    P.local.alloc(n, s);
+    k_translate<<<nblk(n), 256, 0, s>>>(n, P.row_piece.p, refs.p, x.p, P.local.p);
+    PGCP_CUDA(cudaGetLastError());
+    PGCP_CUDA(cudaStreamSynchronize(s));
+    P.have_local = 1;
+    if (!(r.relres <= ctx->opt.tol))
+        fail(PGCP_E_NO_CONVERGENCE, "local (DNCP) solve reached relative residual " + std::to_string(r.relres));
+}
+
+void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P.Nc;
+    P.final.alloc(n, s);
+    k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.welded.p, ctx->opt.warm_start == PGCP_WARM_COLD,
+                                         P.final.p);
+    PGCP_CUDA(cudaGetLastError());
+    SolveResult r = pcg_solve(ctx, P, 0, P.is_bnd.p, P.final.p);
+    P.stats.final_iters = r.iters;
+    P.stats.final_refine = r.refine;
+    P.stats.final_relres = r.relres;
+    P.have_final = 1;
+    const int dim = P.closed ? 3 : 2;
+    DBuf<double> dout;
+    double* o = out;
+    if (host_out) {
+        dout.alloc(dim * P.nv, s);
+        o = dout.p;
+    }
+    DBuf<unsigned long long> mism;
+    mism.alloc(1, s);
+    mism.zero();
+    // vertices in no face stay NaN (all-ones bit pattern)
+    PGCP_CUDA(cudaMemsetAsync(o, 0xff, dim * P.nv * sizeof(double), s));
+    k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.sphere_w_piece, P.final.p,
+                                     dim, o, mism.p);
+    PGCP_CUDA(cudaGetLastError());
+    unsigned long long m = 0;
+    PGCP_CUDA(cudaMemcpyAsync(&m, mism.p, sizeof(m), cudaMemcpyDeviceToHost, s));
+    if (host_out)
+        PGCP_CUDA(cudaMemcpyAsync(out, dout.p, dim * P.nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PGCP_CUDA(cudaStreamSynchronize(s));
+    double md;
+    memcpy(&md, &m, sizeof(md));
+    P.stats.seam_mismatch = md;
+    if (!(r.relres <= ctx->opt.tol))
+        fail(PGCP_E_NO_CONVERGENCE, "final Laplace solve reached relative residual " + std::to_string(r.relres));
+}
+
+}  // namespace pgcp
