@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""PGCP end-to-end throughput on one 1M-vertex synthetic surface per GPU.
+
+A step is one pass of the whole path over one mesh already resident in device
+memory: partition -> cotangent assembly + DNCP (batched PCG) -> partial welds
++ disk map -> final Laplace solve (FP32 PCG inside FP64 refinement, relative
+residual <= 1e-10 per piece and coordinate) -> gathered disk coordinates in
+device memory.  value = vertices / s over K timed steps (CUDA events on the
+library's stream, barrier + synchronize on both sides, max over ranks; L2 is
+flushed with a 256 MB write before every step).  e2e repeats the measurement
+through the one-shot C call with host buffers (copies inside the timed region).
+
+Under torchrun each rank runs its own mesh (different seed): independent
+problems, no collective on the data path, weak scaling.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0
+only), each step a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PGCP end-to-end vertices/s at 1M verts (resid≤1e-10), learned+batched vs plain"
+WORKLOAD = ("1M-vertex Delaunay height field (sum of 8 Gaussians) over the unit disk, "
+            "cut along a 4x2 grid of straight vertex rows into 8 pieces; disk map")
+SAMPLE_N = 150_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_1903_12359_gb300 import meshgen
+from oracle.pipeline import pgcp
+m = meshgen.heightfield_disk_mesh({n}, seed={seed}, nx=4, ny=2)
+t = time.perf_counter()
+r = pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk")
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "nv": m.nv}}))
+"""
+
+
+def oracle_sample(n: int, seed: int) -> dict:
+    """The oracle as it stands, in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, seed=seed)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, bus_id: str | None):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if bus_id:
+            sel = [r for r in rows if r[1].lower().endswith(bus_id.lower()[-7:])]
+            rows = sel or rows
+        if not rows:
+            return None
+        idx0 = rows[0][0]
+        rows = [r for r in rows if r[0] == idx0]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[2]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": num(rows[0][3]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def ncu_traffic(kernel_src: str):
+    """DRAM bytes per PCG launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pcg_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if d.get("source_sha256") != h:
+        return None
+    return d
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    cores = 1
+    times = []
+    nv = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(SAMPLE_N, args.seed)
+        nv = r["nv"]
+        if i >= args.warmup:
+            times.append(r["seconds"])
+    total = sum(times)
+    value = nv * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_nv": nv, "variant": "disk"},
+            "cpu_baseline": {"value": value, "unit": "vertices/s", "cores": cores, "kind": "oracle",
+                             "sample": f"full FP64 oracle pipeline (disk) on a {nv}-vertex mesh of the same "
+                                       f"recipe and 4x2 cut grid, one thread"},
+            "e2e": {"value": value, "unit": "vertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the oracle runs in its own process, started before any GPU work here
+        cpu = oracle_sample(SAMPLE_N, args.seed)
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1903_12359_gb300 import build, meshgen
+    build.build()
+    from paper_1903_12359_gb300 import api
+
+    m = meshgen.heightfield_disk_mesh(args.n, seed=args.seed + rank, nx=4, ny=2)
+    Vd = torch.as_tensor(m.V, device="cuda")
+    Fd = torch.as_tensor(m.F, device="cuda", dtype=torch.int32)
+    Ld = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
+    out = torch.empty((m.nv, 2), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make_ctx(warm):
+        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, warm_start=warm)
+
+    def step(ctx):
+        part = ctx.partition(Vd, Fd, face_labels=Ld)
+        part.local_param()
+        part.weld()
+        part.global_solve(out)
+        st = part.stats
+        part.free()
+        return st
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(ctx, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            step(ctx)
+        barrier()
+        if sampler:
+            sampler.start()
+        l0 = api.launch_count()
+        stream = ctx.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            stats.append(step(ctx))
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = api.launch_count() - l0
+        clocks = sampler.stop(getattr(torch.cuda.get_device_properties(local), "pci_bus_id", None)) if sampler else None
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, launches, clocks
+
+    ctx = make_ctx(api.WARM_WELDMAP)
+    sampler = ClockSampler()
+    ms, stats, launches, clocks = timed(ctx, args.steps, args.warmup, sampler)
+    value = ws * m.nv * args.steps / (ms / 1000.0)
+    # plain form: cold start of the final solve (same pipeline otherwise)
+    ctx_cold = make_ctx(api.WARM_COLD)
+    ms_cold, stats_cold, _, _ = timed(ctx_cold, max(2, args.steps // 2), 1)
+    value_cold = ws * m.nv * max(2, args.steps // 2) / (ms_cold / 1000.0)
+    # end to end through the one-shot C call with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Vh, Fh, Lh = m.V, m.F.astype(np.int32), m.face_labels.astype(np.int32)
+        ctx.run(Vh, Fh, face_labels=Lh, host=True)
+        barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(args.steps):
+            ctx.run(Vh, Fh, face_labels=Lh, host=True)
+        e1.record(ctx.stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        wall = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ws * m.nv * args.steps / (ems / 1000.0), "unit": "vertices/s",
+               "h2d_bytes_per_step": int(Vh.nbytes + Fh.nbytes + Lh.nbytes),
+               "d2h_bytes_per_step": int(m.nv * 2 * 8), "wall_s": wall}
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    pcg_ms = sum(s["pcg_ms"] for s in stats)
+    pcg_bytes = sum(s["pcg_bytes"] for s in stats)
+    pcg_launches = sum(s["pcg_launches"] for s in stats)
+    achieved = pcg_bytes / (pcg_ms / 1000.0) / 1e9 if pcg_ms > 0 else 0.0
+    tr = ncu_traffic(os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg.cu"))
+    roofline = {"kernel": "k_pcg<float,8> (persistent batched PCG)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "frac": achieved / (hbm if hbm else 6800.0),
+                "peak_source": "measured" if hbm else "fallback",
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "algorithmic_bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
+                "avg_launch_ms": pcg_ms / max(pcg_launches, 1), "launches": pcg_launches}
+    s0 = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nv": m.nv, "nf": m.nf, "pieces": s0["K"], "variant": "disk",
+                       "tol": 1e-10, "precision": "FP32 PCG in FP64 refinement", "warm_start": "weld map",
+                       "l2": "flushed before every step (256 MB write)",
+                       "plain_cold_start_value": value_cold,
+                       "learned_warm_start": "not built yet"},
+            "stages_ms": {k: s0[k] for k in ("ms_partition", "ms_assembly", "ms_local", "ms_weld", "ms_final")},
+            "iterations": {"dncp": s0["dncp_iters"], "final": s0["final_iters"],
+                           "final_cold": stats_cold[-1]["final_iters"]},
+            "residual": {"dncp": s0["dncp_relres"], "final": s0["final_relres"]},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu["nv"] / cpu["seconds"], "unit": "vertices/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"full FP64 oracle pipeline (disk) on a {cpu['nv']}-vertex mesh of the "
+                                          f"same recipe and 4x2 cut grid, one thread, {cpu['seconds']:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

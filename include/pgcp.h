@@ -49,7 +49,7 @@ typedef enum { PGCP_WARM_COLD = 0, PGCP_WARM_WELDMAP = 1, PGCP_WARM_LEARNED = 2 
 
 typedef struct {
     int32_t variant;          /* pgcp_variant */
-    int32_t precision;        /* pgcp_precision: PCG arithmetic of both solve stages */
+    int32_t precision;        /* pgcp_precision of the final Laplace solve */
     double  tol;              /* relative residual ||b - A x|| / ||b|| per piece and coordinate */
     int32_t max_iters;        /* PCG iterations per solve (inner solves for FP32_REFINED) */
     int32_t max_refine;       /* outer FP64 refinement steps (FP32_REFINED) */
@@ -57,7 +57,11 @@ typedef struct {
     int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve */
     int32_t interior_map_fp64;/* 1: weld-map the interior in FP64 (else FP32) */
     int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
-    int32_t reserved[7];
+    int32_t local_precision;  /* pgcp_precision of the DNCP solve (default FP64: with two pins its
+                                 conditioning is beyond FP32 refinement) */
+    int32_t spmv_lanes;       /* threads per matrix row in the PCG SpMV: 1, 2, 4 or 8 (autotuner output;
+                                 0 = default 1) */
+    int32_t reserved[5];
 } pgcp_options;
 
 /* Per-call statistics (host struct, filled by pgcp_global_solve). */
@@ -74,6 +78,12 @@ typedef struct {
     double  ms_partition, ms_assembly, ms_local, ms_weld, ms_final;  /* stage times (CUDA events) */
     int64_t nnz;               /* stored entries of all piece Laplacians */
     int64_t n_copies;          /* sum of piece vertex counts */
+    double  pcg_ms;            /* summed duration of the persistent PCG kernel launches (CUDA events
+                                  on the context stream), both solve stages */
+    double  pcg_bytes;         /* algorithmic bytes those launches move: per active free row and
+                                  iteration 4 + 25*T, per stored entry of its row 4 + T (T = 4 or 8) */
+    int32_t pcg_launches;
+    int32_t pad;
 } pgcp_stats;
 
 /* Angle-distortion statistics of a result (Section 5 definition, degrees). */
@@ -98,6 +108,8 @@ pgcp_status pgcp_create(pgcp_ctx** out, const pgcp_options* opt, void* cuda_stre
 pgcp_status pgcp_destroy(pgcp_ctx* ctx);
 pgcp_status pgcp_set_options(pgcp_ctx* ctx, const pgcp_options* opt);
 const char* pgcp_last_error(const pgcp_ctx* ctx);
+/* Number of kernels the library has launched in this process (all contexts). */
+int64_t pgcp_launch_count(void);
 const char* pgcp_status_string(pgcp_status s);
 
 /*
@@ -128,6 +140,9 @@ pgcp_status pgcp_partition_batch(pgcp_ctx* ctx, int32_t n_mesh, const double* co
                                  pgcp_part** out);
 
 pgcp_status pgcp_part_free(pgcp_part* part);
+
+/* Statistics gathered so far by the stages run on this part (host output). */
+pgcp_status pgcp_part_get_stats(const pgcp_part* part, pgcp_stats* st);
 
 /* Sizes of a part (host outputs; any pointer may be NULL). */
 pgcp_status pgcp_part_info(const pgcp_part* part, int32_t* K, int64_t* n_copies, int64_t* nnz,
@@ -196,6 +211,18 @@ pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, 
 pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
                      const int32_t* cut_edges, int64_t n_cut, const int32_t* face_labels,
                      int32_t host_ptrs, double* out, pgcp_stats* st);
+
+/*
+ * Self-test access to the device primitives the partition and the metrics
+ * build on (no counterpart in the paper).  Device pointers, ordered on the
+ * context stream.
+ *  pgcp_selftest_sort: stable sort of n (key, value) pairs by the low `bits`
+ *    bits of key, in place.
+ *  pgcp_selftest_scan: out[i] = sum of in[0..i-1] (int32 in, int64 out);
+ *    *total (host) = sum of all.
+ */
+pgcp_status pgcp_selftest_sort(pgcp_ctx* ctx, uint64_t* keys, int32_t* vals, int64_t n, int32_t bits);
+pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,8 @@ class PgcpError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("variant", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double), ("max_iters", C.c_int32),
                 ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("warm_start", C.c_int32),
-                ("interior_map_fp64", C.c_int32), ("block_rows_log2", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("interior_map_fp64", C.c_int32), ("block_rows_log2", C.c_int32), ("local_precision", C.c_int32),
+                ("spmv_lanes", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -43,7 +44,8 @@ class Stats(C.Structure):
                 ("dncp_refine", C.c_int32), ("final_refine", C.c_int32), ("dncp_relres", C.c_double),
                 ("final_relres", C.c_double), ("seam_mismatch", C.c_double), ("ms_partition", C.c_double),
                 ("ms_assembly", C.c_double), ("ms_local", C.c_double), ("ms_weld", C.c_double),
-                ("ms_final", C.c_double), ("nnz", C.c_int64), ("n_copies", C.c_int64)]
+                ("ms_final", C.c_double), ("nnz", C.c_int64), ("n_copies", C.c_int64), ("pcg_ms", C.c_double),
+                ("pcg_bytes", C.c_double), ("pcg_launches", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,11 +68,13 @@ SIGNATURES = {
     "pgcp_set_options": (C.c_int, [_P, C.POINTER(Options)]),
     "pgcp_last_error": (C.c_char_p, [_P]),
     "pgcp_status_string": (C.c_char_p, [C.c_int]),
+    "pgcp_launch_count": (C.c_int64, []),
     "pgcp_partition": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, C.c_int32,
                                  C.POINTER(_P)]),
     "pgcp_partition_batch": (C.c_int, [_P, C.c_int32, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(_P),
                                        C.POINTER(C.c_int64), C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(_P)]),
     "pgcp_part_free": (C.c_int, [_P]),
+    "pgcp_part_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "pgcp_part_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pgcp_part_get_partition": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -82,6 +86,8 @@ SIGNATURES = {
     "pgcp_metrics": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
     "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
                            C.POINTER(Stats)]),
+    "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
+    "pgcp_selftest_scan": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -101,6 +107,11 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().pgcp_launch_count())
 
 
 def default_options(**kw) -> Options:
@@ -158,6 +169,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    # ---- primitives (self tests)
+    def selftest_sort(self, keys: torch.Tensor, vals: torch.Tensor, bits: int):
+        self.check(load().pgcp_selftest_sort(self.h, _ptr(keys), _ptr(vals), keys.numel(), bits))
+
+    def selftest_scan(self, x: torch.Tensor):
+        out = torch.empty(x.numel(), dtype=torch.int64, device="cuda")
+        tot = C.c_int64()
+        self.check(load().pgcp_selftest_scan(self.h, _ptr(x), _ptr(out), x.numel(), C.byref(tot)))
+        return out, tot.value
 
     # ---- stages
     def partition(self, V, F, cut_edges=None, face_labels=None, closed=False) -> "Part":
@@ -220,6 +241,11 @@ class Part:
                                              C.byref(nw), C.byref(nm)))
         return {"K": K.value, "n_copies": nc.value, "nnz": nnz.value, "n_loop": nl.value, "n_welds": nw.value,
                 "n_mesh": nm.value}
+
+    def get_stats(self):
+        st = Stats()
+        self.ctx.check(load().pgcp_part_get_stats(self.h, C.byref(st)))
+        return st.as_dict()
 
     def partition_arrays(self):
         i = self.info()

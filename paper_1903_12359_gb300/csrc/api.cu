@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <exception>
@@ -25,6 +26,9 @@ struct Thrown : std::exception {
 };
 
 void fail(pgcp_status code, const std::string& msg) { throw Thrown(code, msg); }
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void check_cuda(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return;
@@ -118,8 +122,8 @@ void partition_impl(pgcp_ctx* ctx, int32_t n_mesh, const double* const* V, const
         const MeshInfo& M = P.meshes[b];
         copy_in(P.V, 3 * M.v0, V[b], 3 * M.nv, host, s);
         copy_in(P.F, 3 * M.f0, F[b], 3 * M.nf, host, s);
-        k_offset_faces<<<(unsigned)ceil_div(3 * M.nf, 256), 256, 0, s>>>(P.F.p + 3 * M.f0, 3 * M.nf, (int32_t)M.v0,
-                                                                        M.nv, ctx->err.p);
+        { k_offset_faces<<<(unsigned)ceil_div(3 * M.nf, 256), 256, 0, s>>>(P.F.p + 3 * M.f0, 3 * M.nf, (int32_t)M.v0,
+                                                                        M.nv, ctx->err.p); ::pgcp::note_launch(); }
         if (have_labels) copy_in(d_labels, M.f0, labels[b], M.nf, host, s);
     }
     if (!have_labels && cut && n_cut > 0) {
@@ -166,6 +170,7 @@ void pgcp_default_options(pgcp_options* o) {
     o->warm_start = PGCP_WARM_WELDMAP;
     o->interior_map_fp64 = 0;
     o->block_rows_log2 = 0;
+    o->local_precision = PGCP_FP64;
 }
 
 const char* pgcp_status_string(pgcp_status s) {
@@ -227,6 +232,8 @@ pgcp_status pgcp_set_options(pgcp_ctx* ctx, const pgcp_options* opt) {
     return PGCP_OK;
 }
 
+int64_t pgcp_launch_count(void) { return (int64_t)g_launches.load(); }
+
 const char* pgcp_last_error(const pgcp_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 
 pgcp_status pgcp_partition(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
@@ -258,6 +265,12 @@ pgcp_status pgcp_partition_batch(pgcp_ctx* ctx, int32_t n_mesh, const double* co
 pgcp_status pgcp_part_free(pgcp_part* part) {
     if (!part) return PGCP_E_ARG;
     delete part;
+    return PGCP_OK;
+}
+
+pgcp_status pgcp_part_get_stats(const pgcp_part* part, pgcp_stats* st) {
+    if (!part || !st) return PGCP_E_ARG;
+    *st = part->p.stats;
     return PGCP_OK;
 }
 
@@ -395,6 +408,24 @@ pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* 
     if (s == PGCP_OK) s = pgcp_global_solve(ctx, part, out, host_ptrs, st);
     if (part) pgcp_part_free(part);
     return s;
+}
+
+pgcp_status pgcp_selftest_sort(pgcp_ctx* ctx, uint64_t* keys, int32_t* vals, int64_t n, int32_t bits) {
+    return guard(ctx, [&] {
+        if (!keys || !vals || n < 0 || bits < 0 || bits > 64) fail(PGCP_E_ARG, "bad sort arguments");
+        radix_sort_pairs(keys, vals, n, bits, ctx->stream);
+        PGCP_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total) {
+    return guard(ctx, [&] {
+        if (!in || !out || n < 0) fail(PGCP_E_ARG, "bad scan arguments");
+        int64_t t = 0;
+        exclusive_scan_i32_to_i64(in, out, n, ctx->stream, &t);
+        PGCP_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (total) *total = t;
+    });
 }
 
 }  // extern "C"

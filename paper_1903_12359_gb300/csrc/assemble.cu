@@ -181,21 +181,21 @@ void assemble_laplacian(pgcp_ctx* ctx, Part& P) {
     ctx->err.zero();
     DBuf<double> fw;
     fw.alloc(3 * nf, s);
-    k_face_cot<<<nblk(nf), 256, 0, s>>>(P.cF.p, P.copy_vert.p, P.V.p, nf, fw.p, ctx->err.p);
+    { k_face_cot<<<nblk(nf), 256, 0, s>>>(P.cF.p, P.copy_vert.p, P.V.p, nf, fw.p, ctx->err.p); ::pgcp::note_launch(); }
     DBuf<int32_t> deg, cursor, inc, rowlen;
     DBuf<int64_t> off, rp64;
     deg.alloc(Nc + 1, s);
     deg.zero();
-    k_incidence_count<<<nblk(3 * nf), 256, 0, s>>>(P.cF.p, 3 * nf, deg.p);
+    { k_incidence_count<<<nblk(3 * nf), 256, 0, s>>>(P.cF.p, 3 * nf, deg.p); ::pgcp::note_launch(); }
     off.alloc(Nc + 1, s);
     exclusive_scan_i32_to_i64(deg.p, off.p, Nc + 1, s, nullptr);
     cursor.alloc(Nc, s);
     cursor.zero();
     inc.alloc(3 * nf, s);
-    k_incidence_fill<<<nblk(3 * nf), 256, 0, s>>>(P.cF.p, 3 * nf, off.p, cursor.p, inc.p);
+    { k_incidence_fill<<<nblk(3 * nf), 256, 0, s>>>(P.cF.p, 3 * nf, off.p, cursor.p, inc.p); ::pgcp::note_launch(); }
     rowlen.alloc(Nc + 1, s);
     rowlen.zero();
-    k_row_count<<<nblk(Nc, 128), 128, 0, s>>>(P.cF.p, off.p, inc.p, Nc, rowlen.p, ctx->err.p);
+    { k_row_count<<<nblk(Nc, 128), 128, 0, s>>>(P.cF.p, off.p, inc.p, Nc, rowlen.p, ctx->err.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     rp64.alloc(Nc + 1, s);
     int64_t nnz = 0;
@@ -207,9 +207,9 @@ void assemble_laplacian(pgcp_ctx* ctx, Part& P) {
     P.val64.alloc(nnz, s);
     P.val32.alloc(nnz, s);
     P.diag64.alloc(Nc, s);
-    k_row_fill<<<nblk(Nc, 128), 128, 0, s>>>(P.cF.p, off.p, inc.p, fw.p, Nc, rp64.p, P.row_ptr.p, P.col.p,
-                                             P.val64.p, P.val32.p, P.diag64.p, ctx->err.p);
-    k_set_last<<<1, 1, 0, s>>>(P.row_ptr.p, Nc, nnz);
+    { k_row_fill<<<nblk(Nc, 128), 128, 0, s>>>(P.cF.p, off.p, inc.p, fw.p, Nc, rp64.p, P.row_ptr.p, P.col.p,
+                                             P.val64.p, P.val32.p, P.diag64.p, ctx->err.p); ::pgcp::note_launch(); }
+    { k_set_last<<<1, 1, 0, s>>>(P.row_ptr.p, Nc, nnz); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     uint32_t e = read_errors(ctx);
     if (e & DE_DEGENERATE) fail(PGCP_E_DEGENERATE, "zero-area face");

@@ -135,8 +135,8 @@ void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distort
     cnt.alloc(2, s);
     acc.zero();
     cnt.zero();
-    k_face_metrics<<<(unsigned)std::max<int64_t>(1, ceil_div(nf, 256)), 256, 0, s>>>(
-        P.F.p, nf, P.V.p, U, dim, keys.p, vals.p, acc.p, cnt.p, cnt.p + 1);
+    { k_face_metrics<<<(unsigned)std::max<int64_t>(1, ceil_div(nf, 256)), 256, 0, s>>>(
+        P.F.p, nf, P.V.p, U, dim, keys.p, vals.p, acc.p, cnt.p, cnt.p + 1); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     radix_sort_pairs(keys.p, vals.p, nc, 64, s);
     double h_acc[3];

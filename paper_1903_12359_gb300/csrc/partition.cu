@@ -139,10 +139,21 @@ __global__ void k_union(const uint64_t* __restrict__ keys, const int32_t* __rest
     set_err(err, DE_UNION_LIMIT);
 }
 
+// Read-only walk to the root.  The final compression must not halve paths:
+// another thread's halving could overwrite parent[f] = root with a non-root
+// ancestor after thread f wrote it.
+__device__ int uf_root(volatile int32_t* parent, int x) {
+    while (true) {
+        int px = parent[x];
+        if (px == x) return x;
+        x = px;
+    }
+}
+
 __global__ void k_uf_compress(int32_t* parent, int64_t nf, int32_t* __restrict__ is_root) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
-    int r = uf_find(parent, (int)f);
+    int r = uf_root(parent, (int)f);
     parent[f] = r;
     is_root[f] = (r == (int)f);
 }
@@ -297,20 +308,20 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     PGCP_CUDA(cudaMemsetAsync(keys.p, 0xff, cap * sizeof(uint64_t), s));
     cnt.zero();
     cut.zero();
-    k_edge_insert<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, nf, keys.p, fa.p, fb.p, cnt.p, mask, ctx->err.p);
+    { k_edge_insert<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, nf, keys.p, fa.p, fb.p, cnt.p, mask, ctx->err.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
-    k_edge_check<<<nblk((int64_t)cap), 256, 0, s>>>(keys.p, fa.p, fb.p, cnt.p, d_labels, cut.p, cap, ctx->err.p);
+    { k_edge_check<<<nblk((int64_t)cap), 256, 0, s>>>(keys.p, fa.p, fb.p, cnt.p, d_labels, cut.p, cap, ctx->err.p); ::pgcp::note_launch(); }
     if (!d_labels && d_cut && n_cut > 0)
-        k_mark_cut<<<nblk(n_cut), 256, 0, s>>>(d_cut, n_cut, keys.p, mask, cut.p, nv, ctx->err.p);
+        { k_mark_cut<<<nblk(n_cut), 256, 0, s>>>(d_cut, n_cut, keys.p, mask, cut.p, nv, ctx->err.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     raise_dev_errors(read_errors(ctx));
     // ---- union-find
     DBuf<int32_t> parent, is_root;
     parent.alloc(nf, s);
     is_root.alloc(nf, s);
-    k_iota<<<nblk(nf), 256, 0, s>>>(parent.p, nf);
-    k_union<<<nblk((int64_t)cap), 256, 0, s>>>(keys.p, fa.p, fb.p, cnt.p, cut.p, cap, parent.p, ctx->err.p);
-    k_uf_compress<<<nblk(nf), 256, 0, s>>>(parent.p, nf, is_root.p);
+    { k_iota<<<nblk(nf), 256, 0, s>>>(parent.p, nf); ::pgcp::note_launch(); }
+    { k_union<<<nblk((int64_t)cap), 256, 0, s>>>(keys.p, fa.p, fb.p, cnt.p, cut.p, cap, parent.p, ctx->err.p); ::pgcp::note_launch(); }
+    { k_uf_compress<<<nblk(nf), 256, 0, s>>>(parent.p, nf, is_root.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     DBuf<int64_t> rank;
     rank.alloc(nf, s);
@@ -324,14 +335,14 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     DBuf<int32_t> forder;
     fkey.alloc(nf, s);
     forder.alloc(nf, s);
-    k_label<<<nblk(nf), 256, 0, s>>>(parent.p, rank.p, nf, P.face_label.p, fkey.p, forder.p);
+    { k_label<<<nblk(nf), 256, 0, s>>>(parent.p, rank.p, nf, P.face_label.p, fkey.p, forder.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     int lbits = 1;
     while ((1ll << lbits) < K) ++lbits;
     radix_sort_pairs(fkey.p, forder.p, nf, lbits, s);
     DBuf<int64_t> d_foff;
     d_foff.alloc(K + 1, s);
-    k_segment_starts<<<nblk(nf), 256, 0, s>>>(fkey.p, nf, d_foff.p, 0, 1);
+    { k_segment_starts<<<nblk(nf), 256, 0, s>>>(fkey.p, nf, d_foff.p, 0, 1); ::pgcp::note_launch(); }
     P.foff.assign(K + 1, 0);
     PGCP_CUDA(cudaMemcpyAsync(P.foff.data(), d_foff.p, K * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     // ---- vertex copies by (label, global id)
@@ -339,7 +350,7 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     DBuf<int32_t> cval;
     ckey.alloc(3 * nf, s);
     cval.alloc(3 * nf, s);
-    k_corner_keys<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, P.face_label.p, nf, (uint64_t)nv, ckey.p, cval.p);
+    { k_corner_keys<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, P.face_label.p, nf, (uint64_t)nv, ckey.p, cval.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     int cbits = 1;
     while ((1ull << cbits) < (uint64_t)K * (uint64_t)nv) ++cbits;
@@ -348,7 +359,7 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     DBuf<int64_t> pos;
     flag.alloc(3 * nf, s);
     pos.alloc(3 * nf, s);
-    k_unique_flags<<<nblk(3 * nf), 256, 0, s>>>(ckey.p, 3 * nf, flag.p);
+    { k_unique_flags<<<nblk(3 * nf), 256, 0, s>>>(ckey.p, 3 * nf, flag.p); ::pgcp::note_launch(); }
     int64_t Nc = 0;
     exclusive_scan_i32_to_i64(flag.p, pos.p, 3 * nf, s, &Nc);
     P.Nc = Nc;
@@ -356,11 +367,11 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     ukey.alloc(Nc, s);
     P.copy_vert.alloc(Nc, s);
     P.row_piece.alloc(Nc, s);
-    k_unique_compact<<<nblk(3 * nf), 256, 0, s>>>(ckey.p, flag.p, pos.p, 3 * nf, (uint64_t)nv, ukey.p,
-                                                  P.copy_vert.p, P.row_piece.p);
+    { k_unique_compact<<<nblk(3 * nf), 256, 0, s>>>(ckey.p, flag.p, pos.p, 3 * nf, (uint64_t)nv, ukey.p,
+                                                  P.copy_vert.p, P.row_piece.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     P.d_voff.alloc(K + 1, s);
-    k_segment_starts<<<nblk(Nc), 256, 0, s>>>(ukey.p, Nc, P.d_voff.p, 0, (uint64_t)nv);
+    { k_segment_starts<<<nblk(Nc), 256, 0, s>>>(ukey.p, Nc, P.d_voff.p, 0, (uint64_t)nv); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaMemcpyAsync(P.d_voff.p + K, &P.Nc, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     P.voff.assign(K + 1, 0);
     PGCP_CUDA(cudaMemcpyAsync(P.voff.data(), P.d_voff.p, K * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -370,9 +381,9 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     // ---- faces as copy rows; lowest-label copy of every vertex
     P.cF.alloc(3 * nf, s);
     P.first_copy.alloc(nv, s);
-    k_fill_i32<<<nblk(nv), 256, 0, s>>>(P.first_copy.p, nv, INT_MAX);
-    k_face_rows<<<nblk(nf), 256, 0, s>>>(P.F.p, forder.p, P.face_label.p, nf, ukey.p, P.d_voff.p,
-                                         (uint64_t)nv, P.cF.p, P.first_copy.p);
+    { k_fill_i32<<<nblk(nv), 256, 0, s>>>(P.first_copy.p, nv, INT_MAX); ::pgcp::note_launch(); }
+    { k_face_rows<<<nblk(nf), 256, 0, s>>>(P.F.p, forder.p, P.face_label.p, nf, ukey.p, P.d_voff.p,
+                                         (uint64_t)nv, P.cF.p, P.first_copy.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     // ---- boundary half-edges
     const int64_t hcap = std::max<int64_t>(3 * nf, 16);
@@ -383,8 +394,8 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
     hpiece.alloc(hcap, s);
     counter.alloc(1, s);
     counter.zero();
-    k_boundary_halfedges<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, forder.p, P.face_label.p, P.cF.p, nf, keys.p, fa.p,
-                                                      fb.p, cnt.p, mask, hcap, counter.p, he.p, hpiece.p);
+    { k_boundary_halfedges<<<nblk(3 * nf), 256, 0, s>>>(P.F.p, forder.p, P.face_label.p, P.cF.p, nf, keys.p, fa.p,
+                                                      fb.p, cnt.p, mask, hcap, counter.p, he.p, hpiece.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     unsigned long long nh = 0;
     PGCP_CUDA(cudaMemcpyAsync(&nh, counter.p, sizeof(nh), cudaMemcpyDeviceToHost, s));

@@ -48,6 +48,8 @@ template <> struct V2<double> { using t = double2; };
 
 struct Tile {
     int32_t seg, lo, hi, pad;
+    int32_t frows, fnnz;   // free rows of the tile and their stored entries
+    int32_t pad2, pad3;
 };
 
 template <typename T>
@@ -62,6 +64,7 @@ struct PcgArgs {
     typename V2<T>::t* r;
     typename V2<T>::t* p;
     typename V2<T>::t* q;
+    typename V2<T>::t* z;   // D^-1 r, written in phase 2 (and by the set-up)
     const Tile* __restrict__ tiles;
     int32_t ntiles;
     int32_t nseg;
@@ -74,7 +77,8 @@ struct PcgArgs {
     int32_t* out_iters;   // [1] iterations run
     int32_t max_iters;
     int32_t dncp;
-    int32_t lanes;   // lanes per row in the SpMV (4, 8, 16 or 32)
+    int32_t lanes;   // threads per row in the SpMV (1, 2, 4 or 8)
+    unsigned long long* work;   // [2] free rows and entries of the active tiles, summed over iterations
 };
 
 template <typename T>
@@ -85,180 +89,63 @@ __device__ __forceinline__ bool col_done(const double* RR, const double* THR, in
     return RR[2 * seg + c] <= THR[2 * seg + c];
 }
 
-template <typename T, int LANES>
-__device__ void phase1_tile(const PcgArgs<T>& a, const Tile& t, int k, double* red, unsigned& act_local) {
-    using T2 = typename V2<T>::t;
-    const int nseg = a.nseg;
-    const double* RRk = a.RR + (k % 3) * 2 * nseg;
-    const double* RZk = a.RZ + (k % 3) * 2 * nseg;
-    const double* RZm = a.RZ + ((k + 2) % 3) * 2 * nseg;
-    const int s = t.seg;
-    bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
-    bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
-    if (d0 && d1) return;
-    if (threadIdx.x == 0) {
-        act_local += 1;
-        atomicMax(&a.iters[s], k + 1);
-    }
-    T beta0 = 0, beta1 = 0;
-    if (k > 0) {
-        if (a.dncp) {
-            double num = RZk[2 * s] + RZk[2 * s + 1], den = RZm[2 * s] + RZm[2 * s + 1];
-            beta0 = beta1 = (T)(den != 0.0 ? num / den : 0.0);
-        } else {
-            beta0 = (T)(RZm[2 * s] != 0.0 ? RZk[2 * s] / RZm[2 * s] : 0.0);
-            beta1 = (T)(RZm[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / RZm[2 * s + 1] : 0.0);
-        }
-    }
-    const int lane_g = threadIdx.x & (LANES - 1);
-    const int group = threadIdx.x / LANES;
-    const int ngroups = blockDim.x / LANES;
-    T acc0 = 0, acc1 = 0;   // <p, q> partials (group leaders)
-    // every lane runs the same number of rounds, so the group shuffles are safe
-    for (int base = t.lo; base < t.hi; base += ngroups) {
-        const int row = base + group;
-        const bool valid = row < t.hi;
-        const T di = valid ? a.dinv[row] : (T)0;
-        const bool live = di != (T)0;   // fixed rows and the tail do no work
-        T w0 = 0, w1 = 0;
-        if (live) {
-            const int b = a.rp[row], e = a.rp[row + 1];
-            for (int j = b + lane_g; j < e; j += LANES) {
-                const int c = a.col[j];
-                const T v = a.val[j];
-                const T dc = a.dinv[c];
-                const T2 rc = a.r[c];
-                w0 += v * (dc * rc.x);
-                w1 += v * (dc * rc.y);
-            }
-        }
-#pragma unroll
-        for (int o = LANES / 2; o > 0; o >>= 1) {
-            w0 += __shfl_xor_sync(0xffffffffu, w0, o, LANES);
-            w1 += __shfl_xor_sync(0xffffffffu, w1, o, LANES);
-        }
-        if (live && lane_g == 0) {
-            if (a.dncp) {
-                const int2 pn = a.nb[row];
-                if (pn.x >= 0) {
-                    const T2 rp_ = a.r[pn.x], rn_ = a.r[pn.y];
-                    const T dp = a.dinv[pn.x], dn = a.dinv[pn.y];
-                    w0 -= (T)0.5 * (dn * rn_.y - dp * rp_.y);
-                    w1 += (T)0.5 * (dn * rn_.x - dp * rp_.x);
-                }
-            }
-            const T2 ri = a.r[row];
-            T2 pi = a.p[row], qi = a.q[row];
-            if (!d0) {
-                pi.x = di * ri.x + beta0 * pi.x;
-                qi.x = w0 + beta0 * qi.x;
-                acc0 += pi.x * qi.x;
-            }
-            if (!d1) {
-                pi.y = di * ri.y + beta1 * pi.y;
-                qi.y = w1 + beta1 * qi.y;
-                acc1 += pi.y * qi.y;
-            }
-            a.p[row] = pi;
-            a.q[row] = qi;
-        }
-    }
-    // block reduction -> one atomic per value
-    double v0 = (double)acc0, v1 = (double)acc1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) {
-        red[2 * warp] = v0;
-        red[2 * warp + 1] = v1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0, s1 = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            s0 += red[2 * w];
-            s1 += red[2 * w + 1];
-        }
-        double* PQk = a.PQ + (k % 2) * 2 * nseg;
-        atomicAdd(&PQk[2 * s], s0);
-        atomicAdd(&PQk[2 * s + 1], s1);
-    }
-}
+constexpr int PCG_THREADS = 512;
 
-template <typename T>
-__device__ void phase2_tile(const PcgArgs<T>& a, const Tile& t, int k, double* red) {
-    using T2 = typename V2<T>::t;
-    const int nseg = a.nseg;
-    const double* RRk = a.RR + (k % 3) * 2 * nseg;
-    const double* RZk = a.RZ + (k % 3) * 2 * nseg;
-    const double* PQk = a.PQ + (k % 2) * 2 * nseg;
-    const int s = t.seg;
-    bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
-    bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
-    if (d0 && d1) return;
-    T al0 = 0, al1 = 0;
-    if (a.dncp) {
-        double den = PQk[2 * s] + PQk[2 * s + 1];
-        al0 = al1 = (T)(den != 0.0 ? (RZk[2 * s] + RZk[2 * s + 1]) / den : 0.0);
-    } else {
-        if (!d0) al0 = (T)(PQk[2 * s] != 0.0 ? RZk[2 * s] / PQk[2 * s] : 0.0);
-        if (!d1) al1 = (T)(PQk[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / PQk[2 * s + 1] : 0.0);
-    }
-    T rz0 = 0, rz1 = 0, rr0 = 0, rr1 = 0;
-    for (int row = t.lo + threadIdx.x; row < t.hi; row += blockDim.x) {
-        const T di = a.dinv[row];
-        if (di == (T)0) continue;
-        T2 xi = a.x[row], ri = a.r[row];
-        const T2 pi = a.p[row], qi = a.q[row];
-        xi.x += al0 * pi.x;
-        xi.y += al1 * pi.y;
-        ri.x -= al0 * qi.x;
-        ri.y -= al1 * qi.y;
-        a.x[row] = xi;
-        a.r[row] = ri;
-        rz0 += ri.x * (di * ri.x);
-        rz1 += ri.y * (di * ri.y);
-        rr0 += ri.x * ri.x;
-        rr1 += ri.y * ri.y;
-    }
-    double v[4] = {(double)rz0, (double)rz1, (double)rr0, (double)rr1};
+// Block-sum NV doubles; thread 0 receives the totals in out[].
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* red, double* out) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
     if (lane == 0)
-        for (int i = 0; i < 4; ++i) red[4 * warp + i] = v[i];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[NV * warp + i] = v[i];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sum[4] = {0, 0, 0, 0};
+        for (int i = 0; i < NV; ++i) out[i] = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int i = 0; i < 4; ++i) sum[i] += red[4 * w + i];
-        double* RZn = a.RZ + ((k + 1) % 3) * 2 * nseg;
-        double* RRn = a.RR + ((k + 1) % 3) * 2 * nseg;
-        atomicAdd(&RZn[2 * s], sum[0]);
-        atomicAdd(&RZn[2 * s + 1], sum[1]);
-        atomicAdd(&RRn[2 * s], sum[2]);
-        atomicAdd(&RRn[2 * s + 1], sum[3]);
+            for (int i = 0; i < NV; ++i) out[i] += red[NV * w + i];
     }
 }
 
 template <typename T, int LANES>
-__global__ void __launch_bounds__(256) k_pcg(PcgArgs<T> a) {
+__device__ __forceinline__ void spmv_row(const PcgArgs<T>& a, int row, int lane_g, T& w0, T& w1) {
+    using T2 = typename V2<T>::t;
+    const int b = a.rp[row], e = a.rp[row + 1];
+    for (int j = b + lane_g; j < e; j += LANES) {
+        const int c = a.col[j];
+        const T v = a.val[j];
+        const T2 zc = a.z[c];
+        w0 += v * zc.x;
+        w1 += v * zc.y;
+    }
+}
+
+template <typename T, int LANES>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> a) {
+    using T2 = typename V2<T>::t;
     cg::grid_group grid = cg::this_grid();
-    __shared__ double red[4 * 8];
-    __shared__ unsigned act_s;
+    __shared__ double red[4 * (PCG_THREADS / 32)];
+    __shared__ double tot[4];
     const int nseg = a.nseg;
+    // this block's contiguous range of tiles
+    const int tb = (int)(((int64_t)a.ntiles * blockIdx.x) / gridDim.x);
+    const int te = (int)(((int64_t)a.ntiles * (blockIdx.x + 1)) / gridDim.x);
+    const int lane_g = threadIdx.x & (LANES - 1);
+    const int group = threadIdx.x / LANES;
+    const int ngroups = blockDim.x / LANES;
+    unsigned long long wrows = 0, wnnz = 0;
     int k = 0;
     for (; k < a.max_iters; ++k) {
-        // ---- phase 1
-        if (threadIdx.x == 0) act_s = 0;
-        if (blockIdx.x == 0) {   // reset slots for later phases (see header)
+        const double* RRk = a.RR + (k % 3) * 2 * nseg;
+        const double* RZk = a.RZ + (k % 3) * 2 * nseg;
+        const double* RZm = a.RZ + ((k + 2) % 3) * 2 * nseg;
+        double* PQk = a.PQ + (k % 2) * 2 * nseg;
+        // ---------------- phase 1: p = z + beta p, q = A z + beta q, <p, q>
+        if (blockIdx.x == 0) {   // reset slots used two phases later (see header)
             double* RZz = a.RZ + ((k + 1) % 3) * 2 * nseg;
             double* RRz = a.RR + ((k + 1) % 3) * 2 * nseg;
             for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) {
@@ -266,22 +153,170 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs<T> a) {
                 RRz[i] = 0.0;
             }
         }
-        unsigned act_local = 0;
-        for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) phase1_tile<T, LANES>(a, a.tiles[ti], k, red, act_local);
-        if (threadIdx.x == 0 && act_local) atomicAdd(&a.ACT[k % 3], act_local);
+        int run_seg = -1;
+        double run[2] = {0.0, 0.0};
+        bool any = false;
+        for (int ti = tb; ti < te; ++ti) {
+            const Tile t = a.tiles[ti];
+            const int s = t.seg;
+            const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
+            const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
+            if (d0 && d1) continue;
+            any = true;
+            T beta0 = 0, beta1 = 0;
+            if (k > 0) {
+                if (a.dncp) {
+                    double num = RZk[2 * s] + RZk[2 * s + 1], den = RZm[2 * s] + RZm[2 * s + 1];
+                    beta0 = beta1 = (T)(den != 0.0 ? num / den : 0.0);
+                } else {
+                    beta0 = (T)(RZm[2 * s] != 0.0 ? RZk[2 * s] / RZm[2 * s] : 0.0);
+                    beta1 = (T)(RZm[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / RZm[2 * s + 1] : 0.0);
+                }
+            }
+            T acc0 = 0, acc1 = 0;
+            for (int base = t.lo; base < t.hi; base += ngroups) {
+                const int row = base + group;
+                const bool valid = row < t.hi;
+                const T di = valid ? a.dinv[row] : (T)0;
+                const bool live = di != (T)0;
+                T w0 = 0, w1 = 0;
+                if (live) spmv_row<T, LANES>(a, row, lane_g, w0, w1);
+                if (LANES > 1) {
+#pragma unroll
+                    for (int o = LANES / 2; o > 0; o >>= 1) {
+                        w0 += __shfl_xor_sync(0xffffffffu, w0, o, LANES);
+                        w1 += __shfl_xor_sync(0xffffffffu, w1, o, LANES);
+                    }
+                }
+                if (live && lane_g == 0) {
+                    if (a.dncp) {
+                        const int2 pn = a.nb[row];
+                        if (pn.x >= 0) {
+                            const T2 zp = a.z[pn.x], zn = a.z[pn.y];
+                            w0 -= (T)0.5 * (zn.y - zp.y);
+                            w1 += (T)0.5 * (zn.x - zp.x);
+                        }
+                    }
+                    const T2 zi = a.z[row];
+                    T2 pi = a.p[row], qi = a.q[row];
+                    if (!d0) {
+                        pi.x = zi.x + beta0 * pi.x;
+                        qi.x = w0 + beta0 * qi.x;
+                        acc0 += pi.x * qi.x;
+                    }
+                    if (!d1) {
+                        pi.y = zi.y + beta1 * pi.y;
+                        qi.y = w1 + beta1 * qi.y;
+                        acc1 += pi.y * qi.y;
+                    }
+                    a.p[row] = pi;
+                    a.q[row] = qi;
+                }
+            }
+            double v[2] = {(double)acc0, (double)acc1};
+            block_sum<2>(v, red, tot);
+            if (threadIdx.x == 0) {
+                if (s != run_seg) {
+                    if (run_seg >= 0) {
+                        atomicAdd(&PQk[2 * run_seg], run[0]);
+                        atomicAdd(&PQk[2 * run_seg + 1], run[1]);
+                    }
+                    run_seg = s;
+                    run[0] = tot[0];
+                    run[1] = tot[1];
+                } else {
+                    run[0] += tot[0];
+                    run[1] += tot[1];
+                }
+                wrows += (unsigned long long)t.frows;
+                wnnz += (unsigned long long)t.fnnz;
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (run_seg >= 0) {
+                atomicAdd(&PQk[2 * run_seg], run[0]);
+                atomicAdd(&PQk[2 * run_seg + 1], run[1]);
+            }
+            if (any) *(volatile unsigned*)&a.ACT[k % 3] = 1u;
+        }
         grid.sync();
-        // ---- phase 2
+        // ---------------- phase 2: x += alpha p, r -= alpha q, <r, z>, <r, r>
         if (blockIdx.x == 0) {
             double* PQz = a.PQ + ((k + 1) % 2) * 2 * nseg;
             for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) PQz[i] = 0.0;
             if (threadIdx.x == 0) a.ACT[(k + 1) % 3] = 0;
         }
-        for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) phase2_tile<T>(a, a.tiles[ti], k, red);
+        double* RZn = a.RZ + ((k + 1) % 3) * 2 * nseg;
+        double* RRn = a.RR + ((k + 1) % 3) * 2 * nseg;
+        int run2_seg = -1;
+        double run2[4] = {0, 0, 0, 0};
+        for (int ti = tb; ti < te; ++ti) {
+            const Tile t = a.tiles[ti];
+            const int s = t.seg;
+            const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
+            const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
+            if (d0 && d1) continue;
+            T al0 = 0, al1 = 0;
+            if (a.dncp) {
+                double den = PQk[2 * s] + PQk[2 * s + 1];
+                al0 = al1 = (T)(den != 0.0 ? (RZk[2 * s] + RZk[2 * s + 1]) / den : 0.0);
+            } else {
+                if (!d0) al0 = (T)(PQk[2 * s] != 0.0 ? RZk[2 * s] / PQk[2 * s] : 0.0);
+                if (!d1) al1 = (T)(PQk[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / PQk[2 * s + 1] : 0.0);
+            }
+            T rz0 = 0, rz1 = 0, rr0 = 0, rr1 = 0;
+            for (int row = t.lo + threadIdx.x; row < t.hi; row += blockDim.x) {
+                const T di = a.dinv[row];
+                if (di == (T)0) continue;
+                T2 xi = a.x[row], ri = a.r[row];
+                const T2 pi = a.p[row], qi = a.q[row];
+                xi.x += al0 * pi.x;
+                xi.y += al1 * pi.y;
+                ri.x -= al0 * qi.x;
+                ri.y -= al1 * qi.y;
+                a.x[row] = xi;
+                a.r[row] = ri;
+                T2 zi;
+                zi.x = di * ri.x;
+                zi.y = di * ri.y;
+                a.z[row] = zi;
+                rz0 += ri.x * zi.x;
+                rz1 += ri.y * zi.y;
+                rr0 += ri.x * ri.x;
+                rr1 += ri.y * ri.y;
+            }
+            double v[4] = {(double)rz0, (double)rz1, (double)rr0, (double)rr1};
+            block_sum<4>(v, red, tot);
+            if (threadIdx.x == 0) {
+                if (s != run2_seg) {
+                    if (run2_seg >= 0) {
+                        atomicAdd(&RZn[2 * run2_seg], run2[0]);
+                        atomicAdd(&RZn[2 * run2_seg + 1], run2[1]);
+                        atomicAdd(&RRn[2 * run2_seg], run2[2]);
+                        atomicAdd(&RRn[2 * run2_seg + 1], run2[3]);
+                    }
+                    run2_seg = s;
+                    for (int i = 0; i < 4; ++i) run2[i] = tot[i];
+                } else {
+                    for (int i = 0; i < 4; ++i) run2[i] += tot[i];
+                }
+            }
+        }
+        if (threadIdx.x == 0 && run2_seg >= 0) {
+            atomicAdd(&RZn[2 * run2_seg], run2[0]);
+            atomicAdd(&RZn[2 * run2_seg + 1], run2[1]);
+            atomicAdd(&RRn[2 * run2_seg], run2[2]);
+            atomicAdd(&RRn[2 * run2_seg + 1], run2[3]);
+        }
         grid.sync();
         const unsigned act = *(volatile unsigned*)&a.ACT[k % 3];
         if (act == 0) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.out_iters[0] = k;
+    if (threadIdx.x == 0) {
+        if (wrows) atomicAdd(&a.work[0], wrows);
+        if (wnnz) atomicAdd(&a.work[1], wnnz);
+        if (blockIdx.x == 0) a.out_iters[0] = k;
+    }
 }
 
 // ---------------------------------------------------------------- helpers
@@ -319,13 +354,14 @@ __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __rest
                            const int32_t* __restrict__ col, const TM* __restrict__ val,
                            const double* __restrict__ dinv64, const int2* __restrict__ nb, int dncp,
                            const TX* __restrict__ x, int only_fixed, double2* __restrict__ r_out,
-                           double* __restrict__ RR, double* __restrict__ RZ) {
+                           double* __restrict__ RR, double* __restrict__ RZ, double2* __restrict__ z_out = nullptr) {
     const Tile t = tiles[blockIdx.x];
     double a0 = 0, a1 = 0, z0 = 0, z1 = 0;
     for (int i = t.lo + threadIdx.x; i < t.hi; i += blockDim.x) {
         const double di = dinv64[i];
         if (di == 0.0) {
             if (r_out) r_out[i] = make_double2(0.0, 0.0);
+            if (z_out) z_out[i] = make_double2(0.0, 0.0);
             continue;
         }
         double w0 = 0, w1 = 0;
@@ -348,6 +384,7 @@ __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __rest
         }
         double r0 = -w0, r1 = -w1;
         if (r_out) r_out[i] = make_double2(r0, r1);
+        if (z_out) z_out[i] = make_double2(di * r0, di * r1);
         a0 += r0 * r0;
         a1 += r1 * r1;
         z0 += r0 * (di * r0);
@@ -360,13 +397,15 @@ __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __rest
 
 // <b, b> and <b, D^-1 b> of an FP32 right-hand side, per (piece, coordinate).
 __global__ void k_rhs_stats(const Tile* __restrict__ tiles, const float* __restrict__ dinv,
-                            const float2* __restrict__ b, double* __restrict__ RR, double* __restrict__ RZ) {
+                            const float2* __restrict__ b, double* __restrict__ RR, double* __restrict__ RZ,
+                            float2* __restrict__ z) {
     const Tile t = tiles[blockIdx.x];
     float a0 = 0, a1 = 0, z0 = 0, z1 = 0;
     for (int i = t.lo + threadIdx.x; i < t.hi; i += blockDim.x) {
         const float di = dinv[i];
-        if (di == 0.f) continue;
         const float2 v = b[i];
+        z[i] = make_float2(di * v.x, di * v.y);
+        if (di == 0.f) continue;
         a0 += v.x * v.x;
         a1 += v.y * v.y;
         z0 += v.x * (di * v.x);
@@ -374,6 +413,36 @@ __global__ void k_rhs_stats(const Tile* __restrict__ tiles, const float* __restr
     }
     const int s = t.seg;
     block_add4(a0, a1, z0, z1, &RR[2 * s], &RR[2 * s + 1], &RZ[2 * s], &RZ[2 * s + 1]);
+}
+
+__global__ void k_tile_stats(Tile* tiles, const int32_t* __restrict__ rp, const uint8_t* __restrict__ fixed) {
+    Tile& t = tiles[blockIdx.x];
+    int fr = 0, fz = 0;
+    for (int i = t.lo + threadIdx.x; i < t.hi; i += blockDim.x)
+        if (!fixed[i]) {
+            fr += 1;
+            fz += rp[i + 1] - rp[i];
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        fr += __shfl_xor_sync(0xffffffffu, fr, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    __shared__ int sh[2 * 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[2 * w] = fr;
+        sh[2 * w + 1] = fz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += sh[2 * i];
+            b += sh[2 * i + 1];
+        }
+        t.frows = a;
+        t.fnnz = b;
+    }
 }
 
 __global__ void k_dinv(int64_t n, const double* __restrict__ diag, const uint8_t* __restrict__ fixed,
@@ -408,24 +477,46 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t
 template <typename T, int LANES>
 void launch_pcg(pgcp_ctx* ctx, const PcgArgs<T>& a, int* grid_out) {
     int per_sm = 0;
-    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, LANES>, 256, 0));
+    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, LANES>, PCG_THREADS, 0));
     if (per_sm <= 0) fail(PGCP_E_CUDA, "PCG kernel cannot be resident");
     int grid = std::min<int>(per_sm * ctx->num_sms, a.ntiles);
     grid = std::max(grid, 1);
     *grid_out = grid;
     void* args[] = {(void*)&a};
-    PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_pcg<T, LANES>, dim3(grid), dim3(256), args, 0, ctx->stream));
+    { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_pcg<T, LANES>, dim3(grid), dim3(PCG_THREADS), args, 0, ctx->stream)); ::pgcp::note_launch(); }
 }
 
+// Launch the persistent PCG kernel; its duration (CUDA events on the context
+// stream) and algorithmic bytes go to the part's statistics.
 template <typename T>
-void launch_pcg_lanes(pgcp_ctx* ctx, PcgArgs<T> a) {
+void launch_pcg_lanes(pgcp_ctx* ctx, Part& P, PcgArgs<T> a) {
     int grid = 0;
+    cudaEvent_t e0, e1;
+    PGCP_CUDA(cudaEventCreate(&e0));
+    PGCP_CUDA(cudaEventCreate(&e1));
+    PGCP_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    PGCP_CUDA(cudaEventRecord(e0, ctx->stream));
     switch (a.lanes) {
+        case 2: launch_pcg<T, 2>(ctx, a, &grid); break;
         case 4: launch_pcg<T, 4>(ctx, a, &grid); break;
-        case 16: launch_pcg<T, 16>(ctx, a, &grid); break;
-        case 32: launch_pcg<T, 32>(ctx, a, &grid); break;
-        default: a.lanes = 8; launch_pcg<T, 8>(ctx, a, &grid); break;
+        case 8: launch_pcg<T, 8>(ctx, a, &grid); break;
+        default: a.lanes = 1; launch_pcg<T, 1>(ctx, a, &grid); break;
     }
+    PGCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    unsigned long long w[2] = {0, 0};
+    PGCP_CUDA(cudaMemcpyAsync(w, a.work, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
+    PGCP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PGCP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double Tb = (double)sizeof(T);
+    P.stats.pcg_ms += ms;
+    // per free row and iteration: row pointer 4 B, inverse diagonal T (phase 2),
+    // vectors 2T each: z read (1) and write (1), r r/w (2), p r/w + read (3),
+    // q r/w + read (3), x r/w (2) -> 24T; per stored entry: column 4 B + value T
+    P.stats.pcg_bytes += (double)w[0] * (4.0 + 25.0 * Tb) + (double)w[1] * (4.0 + Tb);
+    P.stats.pcg_launches += 1;
 }
 
 }  // namespace
@@ -436,16 +527,17 @@ void launch_pcg_lanes(pgcp_ctx* ctx, PcgArgs<T> a) {
 // guess; fixed[i] = 1 marks fixed rows.
 SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, double2* x) {
     cudaStream_t s = ctx->stream;
-    const pgcp_options& o = ctx->opt;
+    pgcp_options o = ctx->opt;
+    if (dncp) o.precision = o.local_precision;
     const int64_t n = P.Nc;
     const int S = P.K;
     // tiles: rows of one piece, at most 2^log2 rows each
-    int lg = o.block_rows_log2 > 0 ? o.block_rows_log2 : 11;
+    int lg = o.block_rows_log2 > 0 ? o.block_rows_log2 : 9;
     const int64_t TR = 1ll << lg;
     std::vector<Tile> tiles;
     for (int i = 0; i < S; ++i)
         for (int64_t lo = P.voff[i]; lo < P.voff[i + 1]; lo += TR)
-            tiles.push_back(Tile{i, (int32_t)lo, (int32_t)std::min<int64_t>(lo + TR, P.voff[i + 1]), 0});
+            tiles.push_back(Tile{i, (int32_t)lo, (int32_t)std::min<int64_t>(lo + TR, P.voff[i + 1]), 0, 0, 0, 0, 0});
     DBuf<Tile> d_tiles;
     d_tiles.alloc(tiles.size(), s);
     PGCP_CUDA(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, s));
@@ -453,7 +545,10 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     DBuf<float> dinv32;
     dinv64.alloc(n, s);
     dinv32.alloc(n, s);
-    k_dinv<<<nblk(n), 256, 0, s>>>(n, P.diag64.p, fixed, dinv64.p, dinv32.p);
+    { k_dinv<<<nblk(n), 256, 0, s>>>(n, P.diag64.p, fixed, dinv64.p, dinv32.p); ::pgcp::note_launch(); }
+    { k_tile_stats<<<(unsigned)tiles.size(), 256, 0, s>>>(d_tiles.p, P.row_ptr.p, fixed); ::pgcp::note_launch(); }
+    DBuf<unsigned long long> work;
+    work.alloc(2, s);
     // <b, b> per (piece, coordinate): b = -A x_fixed on free rows
     DBuf<double> BB, RRo, THR, RZ, RR, PQ;
     DBuf<unsigned int> ACT;
@@ -469,8 +564,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     out_it.alloc(1, s);
     BB.zero();
     const unsigned nt = (unsigned)tiles.size();
-    k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
-                                                  dncp, x, 1, nullptr, BB.p, nullptr);
+    { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
+                                                  dncp, x, 1, nullptr, BB.p, nullptr); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     std::vector<double> hBB(2 * S), hRR(2 * S), hTHR(2 * S);
     PGCP_CUDA(cudaMemcpyAsync(hBB.data(), BB.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -500,9 +595,10 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     if (o.precision == PGCP_FP64) {
         // FP64 PCG, restarted from the true residual while recursion drift
         // leaves it above the tolerance
-        DBuf<double2> p, q;
+        DBuf<double2> p, q, z;
         p.alloc(n, s);
         q.alloc(n, s);
+        z.alloc(n, s);
         for (int i = 0; i < 2 * S; ++i) hTHR[i] = tol2 * hBB[i];
         PGCP_CUDA(cudaMemcpyAsync(THR.p, hTHR.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
         for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
@@ -513,26 +609,26 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
             PQ.zero();
             ACT.zero();
             iters.zero();
-            k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                          P.nb.p, dncp, x, 0, r64.p, RR.p, RZ.p);
+            { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
+                                                          P.nb.p, dncp, x, 0, r64.p, RR.p, RZ.p, z.p); ::pgcp::note_launch(); }
             PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RR.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
             PGCP_CUDA(cudaStreamSynchronize(s));
             bool ok = false;
             res.relres = relres_of(hRR, &ok);
             res.refine = outer;
             if (ok) return res;
-            PcgArgs<double> a{n, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p, x, r64.p, p.p, q.p,
+            PcgArgs<double> a{n, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p, x, r64.p, p.p, q.p, z.p,
                               d_tiles.p, (int32_t)tiles.size(), S, RZ.p, RR.p, PQ.p, ACT.p, THR.p, iters.p,
-                              out_it.p, o.max_iters, dncp, 8};
-            launch_pcg_lanes<double>(ctx, a);
+                              out_it.p, o.max_iters, dncp, o.spmv_lanes, work.p};
+            launch_pcg_lanes<double>(ctx, P, a);
             int it = 0;
             PGCP_CUDA(cudaMemcpyAsync(&it, out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
             PGCP_CUDA(cudaStreamSynchronize(s));
             res.iters += it;
         }
         RRo.zero();
-        k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr);
+        { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
+                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
         PGCP_CUDA(cudaStreamSynchronize(s));
         bool ok = false;
@@ -541,7 +637,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         return res;
     }
     // ---- FP32 inner solves inside FP64 refinement
-    DBuf<float2> b32, d32, p32, q32;
+    DBuf<float2> b32, d32, p32, q32, z32;
+    z32.alloc(n, s);
     b32.alloc(n, s);
     d32.alloc(n, s);
     p32.alloc(n, s);
@@ -549,8 +646,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     const double itol2 = o.inner_tol * o.inner_tol;
     for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
         RRo.zero();
-        k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                      P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr);
+        { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
+                                                      P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
         PGCP_CUDA(cudaStreamSynchronize(s));
         bool ok = false;
@@ -569,27 +666,27 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
             }
         }
         PGCP_CUDA(cudaMemcpyAsync(THR.p, hTHR.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
-        k_to_f32<<<nblk(n), 256, 0, s>>>(n, r64.p, b32.p, d32.p, p32.p, q32.p);
+        { k_to_f32<<<nblk(n), 256, 0, s>>>(n, r64.p, b32.p, d32.p, p32.p, q32.p); ::pgcp::note_launch(); }
         RZ.zero();
         RR.zero();
         PQ.zero();
         ACT.zero();
         iters.zero();
         // RZ0, RR0 of the FP32 right-hand side (x = 0 so r = b)
-        k_rhs_stats<<<nt, 256, 0, s>>>(d_tiles.p, dinv32.p, b32.p, RR.p, RZ.p);
-        PcgArgs<float> a{n, P.row_ptr.p, P.col.p, P.val32.p, dinv32.p, P.nb.p, d32.p, b32.p, p32.p, q32.p,
+        { k_rhs_stats<<<nt, 256, 0, s>>>(d_tiles.p, dinv32.p, b32.p, RR.p, RZ.p, z32.p); ::pgcp::note_launch(); }
+        PcgArgs<float> a{n, P.row_ptr.p, P.col.p, P.val32.p, dinv32.p, P.nb.p, d32.p, b32.p, p32.p, q32.p, z32.p,
                          d_tiles.p, (int32_t)tiles.size(), S, RZ.p, RR.p, PQ.p, ACT.p, THR.p, iters.p, out_it.p,
-                         o.max_iters, dncp, 8};
-        launch_pcg_lanes<float>(ctx, a);
+                         o.max_iters, dncp, o.spmv_lanes, work.p};
+        launch_pcg_lanes<float>(ctx, P, a);
         int it = 0;
         PGCP_CUDA(cudaMemcpyAsync(&it, out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        k_add_correction<<<nblk(n), 256, 0, s>>>(n, dinv64.p, d32.p, x);
+        { k_add_correction<<<nblk(n), 256, 0, s>>>(n, dinv64.p, d32.p, x); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaStreamSynchronize(s));
         res.iters += it;
     }
     RRo.zero();
-    k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
-                                                  dncp, x, 0, nullptr, RRo.p, nullptr);
+    { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
+                                                  dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
     PGCP_CUDA(cudaStreamSynchronize(s));
     bool ok = false;

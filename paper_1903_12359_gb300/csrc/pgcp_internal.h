@@ -20,6 +20,8 @@ struct Error {
 
 // Thrown inside the library, turned into a status at the C ABI boundary.
 [[noreturn]] void fail(pgcp_status code, const std::string& msg);
+// Counts every kernel launch of the library (pgcp_launch_count()).
+void note_launch();
 void check_cuda(cudaError_t e, const char* what);
 #define PGCP_CUDA(call) ::pgcp::check_cuda((call), #call)
 

@@ -77,13 +77,13 @@ void scan_impl(const TIn* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* 
     int64_t nt = ceil_div(n, SCAN_TILE);
     DBuf<int64_t> sums;
     sums.alloc(nt + 1, s);
-    k_scan_tiles<TIn><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, out, sums.p, n);
+    { k_scan_tiles<TIn><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, out, sums.p, n); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     if (nt > 1) {
         DBuf<int64_t> offs;
         offs.alloc(nt + 1, s);
         scan_impl<int64_t>(sums.p, offs.p, nt, s, nullptr);
-        k_scan_add<<<(unsigned)nt, 256, 0, s>>>(out, offs.p, n);
+        { k_scan_add<<<(unsigned)nt, 256, 0, s>>>(out, offs.p, n); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         if (total_host) {
             int64_t a = 0, b = 0;
@@ -186,10 +186,10 @@ void radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaSt
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, nb, counts.p);
+        { k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, nb, counts.p); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         exclusive_scan_i64(counts.p, offs.p, 256 * nb, s, nullptr);
-        k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nb, offs.p);
+        { k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nb, offs.p); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);

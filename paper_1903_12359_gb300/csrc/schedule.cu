@@ -91,8 +91,8 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
     P.is_bnd.alloc(P.Nc, s);
     PGCP_CUDA(cudaMemsetAsync(P.nb.p, 0xff, P.Nc * sizeof(int2), s));
     P.is_bnd.zero();
-    k_loop_setup<<<(unsigned)std::max<int64_t>(1, ceil_div(nloop, 256)), 256, 0, s>>>(
-        P.d_loop_rows.p, P.d_loff.p, K, nloop, d_lp.p, P.nb.p, P.is_bnd.p);
+    { k_loop_setup<<<(unsigned)std::max<int64_t>(1, ceil_div(nloop, 256)), 256, 0, s>>>(
+        P.d_loop_rows.p, P.d_loff.p, K, nloop, d_lp.p, P.nb.p, P.is_bnd.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     PGCP_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
 

@@ -117,15 +117,15 @@ void solve_dncp(pgcp_ctx* ctx, Part& P) {
     refs.alloc(P.K, s);
     PGCP_CUDA(cudaMemcpyAsync(pins.p, hp.data(), hp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     PGCP_CUDA(cudaMemcpyAsync(refs.p, hr.data(), hr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    k_dncp_init<<<nblk(n), 256, 0, s>>>(n, fixed.p, x.p);
-    k_dncp_pins<<<nblk(P.K), 256, 0, s>>>(pins.p, P.K, fixed.p, x.p);
+    { k_dncp_init<<<nblk(n), 256, 0, s>>>(n, fixed.p, x.p); ::pgcp::note_launch(); }
+    { k_dncp_pins<<<nblk(P.K), 256, 0, s>>>(pins.p, P.K, fixed.p, x.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     SolveResult r = pcg_solve(ctx, P, 1, fixed.p, x.p);
     P.stats.dncp_iters = r.iters;
     P.stats.dncp_refine = r.refine;
     P.stats.dncp_relres = r.relres;
     P.local.alloc(n, s);
-    k_translate<<<nblk(n), 256, 0, s>>>(n, P.row_piece.p, refs.p, x.p, P.local.p);
+    { k_translate<<<nblk(n), 256, 0, s>>>(n, P.row_piece.p, refs.p, x.p, P.local.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     PGCP_CUDA(cudaStreamSynchronize(s));
     P.have_local = 1;
@@ -137,8 +137,8 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     cudaStream_t s = ctx->stream;
     const int64_t n = P.Nc;
     P.final.alloc(n, s);
-    k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.welded.p, ctx->opt.warm_start == PGCP_WARM_COLD,
-                                         P.final.p);
+    { k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.welded.p, ctx->opt.warm_start == PGCP_WARM_COLD,
+                                         P.final.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     SolveResult r = pcg_solve(ctx, P, 0, P.is_bnd.p, P.final.p);
     P.stats.final_iters = r.iters;
@@ -157,8 +157,8 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     mism.zero();
     // vertices in no face stay NaN (all-ones bit pattern)
     PGCP_CUDA(cudaMemsetAsync(o, 0xff, dim * P.nv * sizeof(double), s));
-    k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.sphere_w_piece, P.final.p,
-                                     dim, o, mism.p);
+    { k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.sphere_w_piece, P.final.p,
+                                     dim, o, mism.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     unsigned long long m = 0;
     PGCP_CUDA(cudaMemcpyAsync(&m, mism.p, sizeof(m), cudaMemcpyDeviceToHost, s));

@@ -844,8 +844,8 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         d_pr.alloc(npts, s);
         d_pi.alloc(npts, s);
         d_pinf.alloc(npts, s);
-        k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
-                                                   d_pi.p, d_pinf.p);
+        { k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
+                                                   d_pi.p, d_pinf.p); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         const int32_t big = 1 << 30;
         PGCP_CUDA(cudaMemcpyAsync(fail_job.p, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -856,7 +856,7 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         int grid = coop_grid(ctx, (const void*)k_weld_phase1, P1_THREADS, npts, 16);
         check_block_sequences(item_seq, grid);
         void* args[] = {(void*)&a};
-        PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_weld_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s));
+        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_weld_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s)); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         uint32_t e = read_errors(ctx);
         if (e & DE_WELD_DOMAIN) {
@@ -902,13 +902,13 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             upload(dra, ra, s); upload(daa, aa, s); upload(dca, ca, s);
             upload(drb, rb, s); upload(dab, ab, s); upload(dcb, cbv, s);
             if (!ra.empty())
-                k_phase2_boundary<<<nblk(ra.size(), 64), 64, 0, s>>>(dra.p, daa.p, dca.p, (int64_t)ra.size(),
+                { k_phase2_boundary<<<nblk(ra.size(), 64), 64, 0, s>>>(dra.p, daa.p, dca.p, (int64_t)ra.size(),
                                                                      d_chains.p, recs.p, arcA.p, P.welded.p,
-                                                                     ctx->err.p);
+                                                                     ctx->err.p); ::pgcp::note_launch(); }
             if (!rb.empty())
-                k_phase2_boundary<<<nblk(rb.size(), 64), 64, 0, s>>>(drb.p, dab.p, dcb.p, (int64_t)rb.size(),
+                { k_phase2_boundary<<<nblk(rb.size(), 64), 64, 0, s>>>(drb.p, dab.p, dcb.p, (int64_t)rb.size(),
                                                                      d_chains.p, recs.p, arcB.p, P.welded.p,
-                                                                     ctx->err.p);
+                                                                     ctx->err.p); ::pgcp::note_launch(); }
             PGCP_CUDA(cudaGetLastError());
             PGCP_CUDA(cudaStreamSynchronize(s));
         }
@@ -953,14 +953,14 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         d_pr.alloc(npts, s);
         d_pi.alloc(npts, s);
         d_pinf.alloc(npts, s);
-        k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
-                                                   d_pi.p, d_pinf.p);
+        { k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
+                                                   d_pi.p, d_pinf.p); ::pgcp::note_launch(); }
         DiskArgs a{d_pr.p, d_pi.p, d_pinf.p, npts, d_item_seq.p, d_seqs.p, (int32_t)seqs.size(), nmax, recs.p,
                    ctx->err.p};
         int grid = coop_grid(ctx, (const void*)k_disk_phase1, P1_THREADS, npts, 16);
         check_block_sequences(item_seq, grid);
         void* args[] = {(void*)&a};
-        PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_disk_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s));
+        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_disk_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s)); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         if (read_errors(ctx) & DE_WELD_DOMAIN)
             fail(PGCP_E_NUMERIC, "disk map: a zipper point left the right half-plane");
@@ -995,9 +995,9 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             upload(d2_arc, p2_arc, s);
             upload(d2_chain, p2_chain, s);
             if (!p2_rows.empty())
-                k_phase2_boundary<<<nblk(p2_rows.size(), 64), 64, 0, s>>>(
+                { k_phase2_boundary<<<nblk(p2_rows.size(), 64), 64, 0, s>>>(
                     d2_rows.p, d2_arc.p, d2_chain.p, (int64_t)p2_rows.size(), d_chains.p, recs.p, img.p,
-                    P.welded.p, ctx->err.p);
+                    P.welded.p, ctx->err.p); ::pgcp::note_launch(); }
             PGCP_CUDA(cudaGetLastError());
             PGCP_CUDA(cudaStreamSynchronize(s));
         }
@@ -1027,14 +1027,14 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         upload(d_flat, flat, s);
         if (!flat.empty()) {
             if (o.interior_map_fp64) {
-                k_interior_map64<<<nblk(P.Nc, 128), 128, 0, s>>>(P.Nc, P.is_bnd.p, P.row_piece.p, d_off.p, d_flat.p,
-                                                                 d_chains.p, recs.p, P.welded.p);
+                { k_interior_map64<<<nblk(P.Nc, 128), 128, 0, s>>>(P.Nc, P.is_bnd.p, P.row_piece.p, d_off.p, d_flat.p,
+                                                                 d_chains.p, recs.p, P.welded.p); ::pgcp::note_launch(); }
             } else {
                 DBuf<RecF> rf;
                 rf.alloc(std::max<int64_t>(nrec, 1), s);
-                k_recs_to_f32<<<nblk(nrec), 256, 0, s>>>(recs.p, rf.p, nrec);
-                k_interior_map<<<nblk(P.Nc, 128), 128, 0, s>>>(P.Nc, P.is_bnd.p, P.row_piece.p, d_off.p, d_flat.p,
-                                                               d_chains.p, rf.p, P.welded.p);
+                { k_recs_to_f32<<<nblk(nrec), 256, 0, s>>>(recs.p, rf.p, nrec); ::pgcp::note_launch(); }
+                { k_interior_map<<<nblk(P.Nc, 128), 128, 0, s>>>(P.Nc, P.is_bnd.p, P.row_piece.p, d_off.p, d_flat.p,
+                                                               d_chains.p, rf.p, P.welded.p); ::pgcp::note_launch(); }
             }
             PGCP_CUDA(cudaGetLastError());
         }

@@ -354,8 +354,52 @@ def heightfield_disk_mesh(N: int, seed: int = 0, nx: int = 4, ny: int = 2, uneve
     V, F, _ = _reorder_spatially(V, F, P2)
     c = V[F, :2].mean(axis=1)
     lab = np.searchsorted(cx, c[:, 0]) + nx * np.searchsorted(cy, c[:, 1])
-    labels = repair_labels(F, _compact_labels(lab.astype(np.int32)))
+    labels = validate_pieces(F, repair_labels(F, _compact_labels(lab.astype(np.int32))))
     return Mesh(V, F, labels, "open", f"heightfield_N{N}_{nx}x{ny}_s{seed}")
+
+
+def _piece_ok(F: np.ndarray, faces: np.ndarray) -> bool:
+    """One piece is a topological disk: one boundary loop, no pinch, V - E + F = 1."""
+    Fi = F[faces]
+    he = np.stack([Fi[:, [0, 1]], Fi[:, [1, 2]], Fi[:, [2, 0]]], axis=1).reshape(-1, 2).astype(np.int64)
+    a, b = np.minimum(he[:, 0], he[:, 1]), np.maximum(he[:, 0], he[:, 1])
+    nv = int(Fi.max()) + 1
+    key = a * nv + b
+    uk, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+    bnd = he[cnt[inv] == 1]
+    if bnd.shape[0] == 0 or np.unique(bnd[:, 0]).size != bnd.shape[0]:
+        return False
+    nxt = dict(zip(bnd[:, 0].tolist(), bnd[:, 1].tolist()))
+    start = bnd[0, 0]
+    v, n = nxt[start], 1
+    while v != start and n <= len(nxt):
+        v = nxt.get(v, start)
+        n += 1
+    if n != len(nxt):
+        return False
+    return np.unique(Fi).size - uk.size + Fi.shape[0] == 1
+
+
+def validate_pieces(F: np.ndarray, labels: np.ndarray, max_rounds: int = 64) -> np.ndarray:
+    """Merge every piece that is not a topological disk into the neighbour it
+    shares most edges with (input-generation step; guards against rare
+    triangulations where a cut row is crossed)."""
+    labels = _compact_labels(labels)
+    nv = int(F.max()) + 1
+    f0, f1, _, _ = _interior_edge_pairs(F, nv)
+    for _ in range(max_rounds):
+        bad = [L for L in range(int(labels.max()) + 1) if not _piece_ok(F, np.nonzero(labels == L)[0])]
+        if not bad:
+            return labels
+        L = bad[0]
+        m0 = (labels[f0] == L) & (labels[f1] != L)
+        m1 = (labels[f1] == L) & (labels[f0] != L)
+        nb = np.concatenate([labels[f1[m0]], labels[f0[m1]]])
+        if nb.size == 0:
+            raise RuntimeError("isolated piece")
+        labels[labels == L] = np.bincount(nb).argmax()
+        labels = repair_labels(F, _compact_labels(labels))
+    raise RuntimeError("piece validation did not converge")
 
 
 def _compact_labels(lab: np.ndarray) -> np.ndarray:
@@ -430,7 +474,7 @@ def icosphere_sh_mesh(subdiv: int = 8, seed: int = 0, lmax: int = 6, amp: float 
     Vs = U / np.linalg.norm(U, axis=1, keepdims=True)
     c = Vs[F].mean(axis=1)
     lab = (c[:, 0] < 0).astype(np.int32) + 2 * (c[:, 1] < 0) + 4 * (c[:, 2] < 0)
-    labels = repair_labels(F, lab.astype(np.int32))
+    labels = validate_pieces(F, repair_labels(F, lab.astype(np.int32)))
     return Mesh(U, F, labels, "closed", f"icosphere_sd{subdiv}_s{seed}")
 
 

@@ -212,3 +212,16 @@ def test_one_shot_host_io(api):
     assert isinstance(out_h, np.ndarray) and out_h.shape == (m.nv, 2)
     assert np.abs(out_h - out_d.cpu().numpy()).max() < 1e-10
     assert st["final_relres"] <= 1e-12
+
+
+@pytest.mark.slow
+def test_partition_full_size_bit_exact(api):
+    """The 1M-vertex workload: partition, vertex lists and loops bit-exact."""
+    m = meshgen.heightfield_disk_mesh(1_000_000, seed=0, nx=4, ny=2)
+    ctx = _ctx(api, "disk")
+    part = ctx.partition(m.V, m.F, face_labels=m.face_labels)
+    fl, voff, verts, loff, loops = [t.cpu().numpy() for t in part.partition_arrays()]
+    P = o_partition(m.V, m.F, face_labels=m.face_labels)
+    assert np.array_equal(fl, P.face_label)
+    assert np.array_equal(verts, np.concatenate(P.verts))
+    assert np.array_equal(loops, np.concatenate(P.loops))
