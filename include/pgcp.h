@@ -98,7 +98,7 @@ typedef struct {
 typedef struct pgcp_ctx pgcp_ctx;    /* opaque; one per CUDA stream */
 typedef struct pgcp_part pgcp_part;  /* opaque; partition + all per-piece device state */
 
-/* Default options: DISK, FP32_REFINED, tol 1e-10, 20000 iterations, 8 refinement
+/* Default options: DISK, FP32_REFINED, tol 1e-10, 200000 iterations, 8 refinement
  * steps, inner_tol 1e-4, weld-map warm start, FP32 interior map. */
 void pgcp_default_options(pgcp_options* opt);
 

@@ -164,7 +164,7 @@ void pgcp_default_options(pgcp_options* o) {
     o->variant = PGCP_DISK;
     o->precision = PGCP_FP32_REFINED;
     o->tol = 1e-10;
-    o->max_iters = 20000;
+    o->max_iters = 200000;
     o->max_refine = 8;
     o->inner_tol = 1e-4;
     o->warm_start = PGCP_WARM_WELDMAP;

@@ -111,6 +111,10 @@ __device__ __forceinline__ void block_sum(double* v, double* red, double* out) {
     }
 }
 
+// x != 0 without an FP64 compare (integer test of the bit pattern; -0 never occurs)
+__device__ __forceinline__ bool nonzero(double x) { return __double_as_longlong(x) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return __float_as_int(x) != 0; }
+
 template <typename T, int LANES>
 __device__ __forceinline__ void spmv_row(const PcgArgs<T>& a, int row, int lane_g, T& w0, T& w1) {
     using T2 = typename V2<T>::t;
@@ -130,6 +134,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> a) {
     cg::grid_group grid = cg::this_grid();
     __shared__ double red[4 * (PCG_THREADS / 32)];
     __shared__ double tot[4];
+    __shared__ double sc[2];
+    __shared__ int sflag[2];
     const int nseg = a.nseg;
     // this block's contiguous range of tiles
     const int tb = (int)(((int64_t)a.ntiles * blockIdx.x) / gridDim.x);
@@ -159,26 +165,39 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> a) {
         for (int ti = tb; ti < te; ++ti) {
             const Tile t = a.tiles[ti];
             const int s = t.seg;
-            const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
-            const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
-            if (d0 && d1) continue;
-            any = true;
-            T beta0 = 0, beta1 = 0;
-            if (k > 0) {
-                if (a.dncp) {
-                    double num = RZk[2 * s] + RZk[2 * s + 1], den = RZm[2 * s] + RZm[2 * s + 1];
-                    beta0 = beta1 = (T)(den != 0.0 ? num / den : 0.0);
-                } else {
-                    beta0 = (T)(RZm[2 * s] != 0.0 ? RZk[2 * s] / RZm[2 * s] : 0.0);
-                    beta1 = (T)(RZm[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / RZm[2 * s + 1] : 0.0);
+            // the tile's scalars, computed once (FP64 divisions are expensive here)
+            if (threadIdx.x == 0) {
+                const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
+                const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
+                double b0 = 0.0, b1 = 0.0;
+                if (k > 0) {
+                    if (a.dncp) {
+                        double num = RZk[2 * s] + RZk[2 * s + 1], den = RZm[2 * s] + RZm[2 * s + 1];
+                        b0 = b1 = den != 0.0 ? num / den : 0.0;
+                    } else {
+                        b0 = RZm[2 * s] != 0.0 ? RZk[2 * s] / RZm[2 * s] : 0.0;
+                        b1 = RZm[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / RZm[2 * s + 1] : 0.0;
+                    }
                 }
+                sc[0] = b0;
+                sc[1] = b1;
+                sflag[0] = d0;
+                sflag[1] = d1;
             }
+            __syncthreads();
+            const bool d0 = sflag[0], d1 = sflag[1];
+            const T beta0 = (T)sc[0], beta1 = (T)sc[1];
+            if (d0 && d1) {
+                __syncthreads();   // everyone has read the scalars before they change
+                continue;
+            }
+            any = true;
             T acc0 = 0, acc1 = 0;
             for (int base = t.lo; base < t.hi; base += ngroups) {
                 const int row = base + group;
                 const bool valid = row < t.hi;
                 const T di = valid ? a.dinv[row] : (T)0;
-                const bool live = di != (T)0;
+                const bool live = nonzero(di);
                 T w0 = 0, w1 = 0;
                 if (live) spmv_row<T, LANES>(a, row, lane_g, w0, w1);
                 if (LANES > 1) {
@@ -253,21 +272,31 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> a) {
         for (int ti = tb; ti < te; ++ti) {
             const Tile t = a.tiles[ti];
             const int s = t.seg;
-            const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
-            const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
-            if (d0 && d1) continue;
-            T al0 = 0, al1 = 0;
-            if (a.dncp) {
-                double den = PQk[2 * s] + PQk[2 * s + 1];
-                al0 = al1 = (T)(den != 0.0 ? (RZk[2 * s] + RZk[2 * s + 1]) / den : 0.0);
-            } else {
-                if (!d0) al0 = (T)(PQk[2 * s] != 0.0 ? RZk[2 * s] / PQk[2 * s] : 0.0);
-                if (!d1) al1 = (T)(PQk[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / PQk[2 * s + 1] : 0.0);
+            if (threadIdx.x == 0) {
+                const bool d0 = col_done(RRk, a.THR, nseg, s, 0, a.dncp);
+                const bool d1 = col_done(RRk, a.THR, nseg, s, 1, a.dncp);
+                double al0 = 0.0, al1 = 0.0;
+                if (a.dncp) {
+                    double den = PQk[2 * s] + PQk[2 * s + 1];
+                    al0 = al1 = den != 0.0 ? (RZk[2 * s] + RZk[2 * s + 1]) / den : 0.0;
+                } else {
+                    if (!d0) al0 = PQk[2 * s] != 0.0 ? RZk[2 * s] / PQk[2 * s] : 0.0;
+                    if (!d1) al1 = PQk[2 * s + 1] != 0.0 ? RZk[2 * s + 1] / PQk[2 * s + 1] : 0.0;
+                }
+                sc[0] = al0;
+                sc[1] = al1;
+                sflag[0] = d0 && d1;
+            }
+            __syncthreads();
+            const T al0 = (T)sc[0], al1 = (T)sc[1];
+            if (sflag[0]) {
+                __syncthreads();
+                continue;
             }
             T rz0 = 0, rz1 = 0, rr0 = 0, rr1 = 0;
             for (int row = t.lo + threadIdx.x; row < t.hi; row += blockDim.x) {
                 const T di = a.dinv[row];
-                if (di == (T)0) continue;
+                if (!nonzero(di)) continue;
                 T2 xi = a.x[row], ri = a.r[row];
                 const T2 pi = a.p[row], qi = a.q[row];
                 xi.x += al0 * pi.x;
