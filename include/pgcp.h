@@ -203,6 +203,32 @@ pgcp_status pgcp_global_solve(pgcp_ctx* ctx, pgcp_part* part, double* out, int32
 pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met);
 
 /*
+ * pgcp_metrics without any device allocation.  Library plumbing: the paper has
+ * no counterpart.  For callers that must not allocate device memory, because
+ * their device memory is held by another allocator or because an allocation
+ * may fail or synchronise at a point where they cannot afford that.
+ *
+ * Same arguments, results and error codes as pgcp_metrics (sums are
+ * accumulated with atomics, so mean and sd may differ from it in the last
+ * bits; order statistics, max, flips and max |mu| are identical).  All device
+ * scratch is one fixed static array inside the library (about 20 MB, sized
+ * for PGCP_METRICS_NOALLOC_MAX_FACES faces); a part with more faces returns
+ * PGCP_E_ARG with a message naming the limit, and pgcp_metrics serves it.
+ *
+ * The context's device must be current (else PGCP_E_ARG).  The first call on a
+ * device looks up the scratch array's address (cudaGetSymbolAddress, which may
+ * load the library's module on that device) and caches it; make that first
+ * call before any stream capture on the device.  The sums, max and counters
+ * in the scratch are cleared on the stream at the start of every call; the
+ * rest is fully overwritten before it is read.  The scratch is shared by every
+ * context on the device: calls that overlap in time (from several host threads,
+ * or on several streams without ordering between them) race on it and give
+ * wrong results.  The call synchronises its context's stream before returning.
+ */
+#define PGCP_METRICS_NOALLOC_MAX_FACES 262144
+pgcp_status pgcp_metrics_noalloc(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met);
+
+/*
  * One-shot convenience: partition + local_param + weld + global_solve.
  * variant selects the output (free: [nv*2], disk: [nv*2], sphere: [nv*3]).
  * host_ptrs = 1: V, F, cut_edges and out are host pointers (the copies are

@@ -16,6 +16,7 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpgcp.so")
+METRICS_NOALLOC_MAX_FACES = 262144   # PGCP_METRICS_NOALLOC_MAX_FACES
 
 FREE, DISK, SPHERE = 0, 1, 2
 FP64, FP32_REFINED = 0, 1
@@ -84,6 +85,7 @@ SIGNATURES = {
     "pgcp_weld": (C.c_int, [_P, _P]),
     "pgcp_global_solve": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Stats)]),
     "pgcp_metrics": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
+    "pgcp_metrics_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
     "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
                            C.POINTER(Stats)]),
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
@@ -292,6 +294,14 @@ class Part:
     def metrics(self, U):
         m = Distortion()
         self.ctx.check(load().pgcp_metrics(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
+        return m.as_dict()
+
+    def metrics_noalloc(self, U):
+        """pgcp_metrics_noalloc: the same statistics with no device allocation,
+        for callers that must not allocate (parts of at most
+        METRICS_NOALLOC_MAX_FACES faces; calls must not overlap in time)."""
+        m = Distortion()
+        self.ctx.check(load().pgcp_metrics_noalloc(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
         return m.as_dict()
 
     def free(self):

@@ -397,6 +397,16 @@ pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, 
     });
 }
 
+pgcp_status pgcp_metrics_noalloc(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met) {
+    return guard(ctx, [&] {
+        if (!ctx || !part || !U || !met) fail(PGCP_E_ARG, "null argument");
+        static_assert(PGCP_METRICS_NOALLOC_MAX_FACES == (1 << 18), "header limit and library limit differ");
+        if (metrics_noalloc_max_faces() != PGCP_METRICS_NOALLOC_MAX_FACES)
+            fail(PGCP_E_ARG, "allocation-free metrics: header limit and library limit differ");
+        compute_metrics_noalloc(ctx, part->p, U, met);
+    });
+}
+
 pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
                      const int32_t* cut_edges, int64_t n_cut, const int32_t* face_labels, int32_t host_ptrs,
                      double* out, pgcp_stats* st) {

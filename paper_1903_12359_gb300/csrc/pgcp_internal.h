@@ -186,6 +186,11 @@ void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaS
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
 void radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s);
 uint32_t read_errors(pgcp_ctx* ctx);
+// The same sort and scan on caller-provided device workspace (no allocation).
+int64_t sort_ws_counts(int64_t n);   // int64 entries needed for `counts` and for `offs`
+void scan_noalloc(const int64_t* in, int64_t* out, int64_t n, int64_t* ws, int64_t ws_len, cudaStream_t s);
+void radix_sort_pairs_noalloc(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s, uint64_t* k2,
+                              int32_t* v2, int64_t* counts, int64_t* offs, int64_t* scan_ws, int64_t scan_ws_len);
 
 // ------------------------------------------------------------------ stages
 
@@ -204,6 +209,9 @@ void solve_dncp(pgcp_ctx* ctx, Part& P);
 void run_welds(pgcp_ctx* ctx, Part& P);
 void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out);
 void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
+// Same statistics on a fixed device-side scratch array; no allocation.
+void compute_metrics_noalloc(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
+int64_t metrics_noalloc_max_faces();
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -200,6 +200,47 @@ void radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaSt
     }
 }
 
+// ---- variants on caller-provided workspace (no allocation)
+
+int64_t sort_ws_counts(int64_t n) { return 256 * ceil_div(std::max<int64_t>(n, 1), RS_TILE); }
+
+void scan_noalloc(const int64_t* in, int64_t* out, int64_t n, int64_t* ws, int64_t ws_len, cudaStream_t s) {
+    // two levels: tile sums [nt], their scan [nt]; nt must fit one tile
+    const int64_t nt = ceil_div(n, SCAN_TILE);
+    if (nt > SCAN_TILE || 2 * (nt + 1) + 2 > ws_len) fail(PGCP_E_ARG, "scan workspace too small");
+    int64_t* sums = ws;
+    int64_t* offs = ws + nt + 1;
+    int64_t* top = ws + 2 * (nt + 1);
+    { k_scan_tiles<int64_t><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, out, sums, n); ::pgcp::note_launch(); }
+    if (nt > 1) {
+        { k_scan_tiles<int64_t><<<1, SCAN_THREADS, 0, s>>>(sums, offs, top, nt); ::pgcp::note_launch(); }
+        { k_scan_add<<<(unsigned)nt, 256, 0, s>>>(out, offs, n); ::pgcp::note_launch(); }
+    }
+    PGCP_CUDA(cudaGetLastError());
+}
+
+void radix_sort_pairs_noalloc(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s, uint64_t* k2,
+                              int32_t* v2, int64_t* counts, int64_t* offs, int64_t* scan_ws, int64_t scan_ws_len) {
+    if (n <= 1 || bits <= 0) return;
+    const int64_t nb = ceil_div(n, RS_TILE);
+    uint64_t *ka = keys, *kb = k2;
+    int32_t *va = vals, *vb = v2;
+    const int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        { k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, nb, counts); ::pgcp::note_launch(); }
+        scan_noalloc(counts, offs, 256 * nb, scan_ws, scan_ws_len, s);
+        { k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nb, offs); ::pgcp::note_launch(); }
+        PGCP_CUDA(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        PGCP_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        PGCP_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
 uint32_t read_errors(pgcp_ctx* ctx) {
     uint32_t e = 0;
     PGCP_CUDA(cudaMemcpyAsync(&e, ctx->err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
