@@ -1,0 +1,60 @@
+"""Fixed, short workloads for kernel profiling.
+
+`dncp`  partition + local DNCP solves of the 1M-vertex height-field disk mesh
+        (4x2 cut grid) with the PCG capped at --max-iters iterations, so that one
+        launch of the persistent PCG kernel lasts a fraction of a second.  The
+        capped solve ends with PGCP_E_NO_CONVERGENCE, which is expected here
+        and reported, not raised.
+`final` the whole pipeline at --n vertices (final solve included).
+
+Usage: python -m paper_1903_12359_gb300.profile_cases dncp --n 1000000 --max-iters 300
+"""
+import argparse
+import json
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["dncp", "final"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--max-iters", type=int, default=300)
+    a = ap.parse_args(argv)
+    import torch
+    from paper_1903_12359_gb300 import api, build, meshgen
+    build.build()
+    m = meshgen.heightfield_disk_mesh(a.n, seed=a.seed, nx=4, ny=2)
+    V = torch.as_tensor(m.V, device="cuda")
+    F = torch.as_tensor(m.F, device="cuda", dtype=torch.int32)
+    L = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
+    if a.case == "dncp":
+        ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, max_iters=a.max_iters,
+                          max_refine=1)
+        part = ctx.partition(V, F, face_labels=L)
+        try:
+            part.local_param()
+            status = "OK"
+        except api.PgcpError as e:
+            if e.code != "NO_CONVERGENCE":
+                raise
+            status = "NO_CONVERGENCE (capped, expected)"
+        torch.cuda.synchronize()
+        st = part.get_stats()
+        print(json.dumps({"case": "dncp", "nv": m.nv, "status": status, "dncp_iters": st["dncp_iters"],
+                          "pcg_ms": st["pcg_ms"], "pcg_bytes": st["pcg_bytes"],
+                          "pcg_launches": st["pcg_launches"]}))
+    else:
+        ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10)
+        part = ctx.partition(V, F, face_labels=L)
+        part.local_param()
+        part.weld()
+        part.global_solve()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "final", "nv": m.nv, **{k: part.stats[k] for k in
+                                                          ("dncp_iters", "final_iters", "pcg_ms")}}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
