@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cold", action="store_true", help="skip the cold-start comparison")
+    ap.add_argument("--local-precision", type=int, default=2,
+                    help="DNCP solve: 0 FP64 PCG, 2 double-float PCG in FP64 refinement")
     return ap.parse_args()
 
 
@@ -149,7 +151,7 @@ def measured_peaks():
         return {}
 
 
-def ncu_traffic(kernel_src: str):
+def ncu_traffic(kernel: str, kernel_src: str):
     """DRAM bytes per PCG iteration from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "pcg_traffic.json")
@@ -158,9 +160,10 @@ def ncu_traffic(kernel_src: str):
     except (OSError, ValueError):
         return None
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if d.get("source_sha256") != h:
-        return None
-    return d
+    for e in (d if isinstance(d, list) else [d]):
+        if e.get("kernel") == kernel and e.get("source_sha256") == h:
+            return e
+    return None
 
 
 # ---------------------------------------------------------------- reference arm
@@ -219,7 +222,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def make_ctx(warm):
-        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, warm_start=warm)
+        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, warm_start=warm,
+                           local_precision=args.local_precision)
 
     def step(ctx):
         part = ctx.partition(Vd, Fd, face_labels=Ld)
@@ -308,9 +312,13 @@ def main():
     step_pcg_ms = sum(s["pcg_ms"] for s in stats)
     dncp_iters = sum(s["dncp_iters"] for s in stats)
     achieved = pcg_bytes / (pcg_ms / 1000.0) / 1e9 if pcg_ms > 0 else 0.0
-    tr = ncu_traffic(os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg.cu"))
+    df = args.local_precision == 2
+    kname = "k_pcg_df" if df else "k_pcg<double,1>"
+    tr = ncu_traffic(kname, os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg_df.cu" if df else "pcg.cu"))
     peak = hbm if hbm else 6800.0
-    roofline = {"kernel": "k_pcg<double,1> (persistent batched FP64 PCG, local DNCP solves)", "bound": "hbm",
+    kdesc = ("k_pcg_df (persistent batched double-float PCG in FP64 refinement, local DNCP solves)" if df
+             else "k_pcg<double,1> (persistent batched FP64 PCG, local DNCP solves)")
+    roofline = {"kernel": kdesc, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (burst copy)" if hbm else "fallback",
                 "traffic": (tr["dram_bytes_per_iteration"] * dncp_iters / max(pcg_launches, 1) if tr else None),
@@ -324,7 +332,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nv": m.nv, "nf": m.nf, "pieces": s0["K"], "variant": "disk",
-                       "tol": 1e-10, "precision": "FP32 PCG in FP64 refinement", "warm_start": "weld map",
+                       "tol": 1e-10, "precision": "final solve: FP32 PCG in FP64 refinement; DNCP: " +
+                       ("double-float PCG in FP64 refinement" if df else "FP64 PCG"), "warm_start": "weld map",
                        "l2": "flushed before every step (256 MB write)",
                        "plain_cold_start_value": value_cold,
                        "learned_warm_start": "not built yet"},

@@ -44,7 +44,11 @@ typedef enum {
 } pgcp_status;
 
 typedef enum { PGCP_FREE = 0, PGCP_DISK = 1, PGCP_SPHERE = 2 } pgcp_variant;
-typedef enum { PGCP_FP64 = 0, PGCP_FP32_REFINED = 1 } pgcp_precision;
+/* FP64: FP64 Jacobi-PCG.  FP32_REFINED: FP32 PCG inside FP64 iterative
+ * refinement.  DF64_REFINED: double-float (hi + lo float pairs, ~48 bits) PCG
+ * on the symmetrically Jacobi-scaled system inside FP64 iterative refinement;
+ * runs on the FP32 pipe.  Every mode stops on the FP64 residual. */
+typedef enum { PGCP_FP64 = 0, PGCP_FP32_REFINED = 1, PGCP_DF64_REFINED = 2 } pgcp_precision;
 typedef enum { PGCP_WARM_COLD = 0, PGCP_WARM_WELDMAP = 1, PGCP_WARM_LEARNED = 2 } pgcp_warm_start;
 
 typedef struct {
@@ -57,8 +61,8 @@ typedef struct {
     int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve */
     int32_t interior_map_fp64;/* 1: weld-map the interior in FP64 (else FP32) */
     int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
-    int32_t local_precision;  /* pgcp_precision of the DNCP solve (default FP64: with two pins its
-                                 conditioning is beyond FP32 refinement) */
+    int32_t local_precision;  /* pgcp_precision of the DNCP solve (FP32_REFINED stalls: with two pins
+                                 its conditioning is beyond FP32 refinement) */
     int32_t spmv_lanes;       /* threads per matrix row in the PCG SpMV: 1, 2, 4 or 8 (autotuner output;
                                  0 = default 1) */
     int32_t reserved[5];

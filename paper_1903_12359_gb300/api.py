@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpgcp.so")
 METRICS_NOALLOC_MAX_FACES = 262144   # PGCP_METRICS_NOALLOC_MAX_FACES
 
 FREE, DISK, SPHERE = 0, 1, 2
-FP64, FP32_REFINED = 0, 1
+FP64, FP32_REFINED, DF64_REFINED = 0, 1, 2
 WARM_COLD, WARM_WELDMAP, WARM_LEARNED = 0, 1, 2
 
 STATUS = {0: "OK", 1: "ARG", 2: "CUDA", 3: "OOM", 4: "NONMANIFOLD", 5: "TOPOLOGY", 6: "SCHEDULE",

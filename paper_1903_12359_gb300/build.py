@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpgcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["primitives.cu", "partition.cu", "schedule.cu", "assemble.cu", "pcg.cu", "weld.cu", "solve.cu",
+SOURCES = ["primitives.cu", "partition.cu", "schedule.cu", "assemble.cu", "pcg.cu", "pcg_df.cu", "weld.cu", "solve.cu",
            "metrics.cu", "api.cu"]
 NO_FMA = {"weld.cu"}
 

@@ -621,6 +621,41 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     };
     DBuf<double2> r64;
     r64.alloc(n, s);
+    if (o.precision == PGCP_DF64_REFINED) {
+        // double-float inner solves to the final tolerance, FP64 residual outside
+        DfSystem D;
+        df_build(ctx, P, dncp, fixed, D);
+        for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
+            RRo.zero();
+            { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
+                                                          P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr); ::pgcp::note_launch(); }
+            PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
+            PGCP_CUDA(cudaStreamSynchronize(s));
+            bool ok = false;
+            res.relres = relres_of(hRR, &ok);
+            res.refine = outer;
+            if (ok) return res;
+            for (int i = 0; i < S; ++i) {
+                for (int c = 0; c < 2; ++c) {
+                    const int j = 2 * i + c;
+                    bool conv;
+                    if (dncp) conv = hRR[2 * i] + hRR[2 * i + 1] <= tol2 * (hBB[2 * i] + hBB[2 * i + 1]);
+                    else conv = hRR[j] <= tol2 * hBB[j];
+                    hTHR[j] = conv ? INFINITY : 0.25 * tol2 * hBB[j];
+                }
+            }
+            res.iters += df_solve(ctx, P, D, r64.p, x, hTHR, o.max_iters);
+        }
+        RRo.zero();
+        { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
+                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
+        PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PGCP_CUDA(cudaStreamSynchronize(s));
+        bool ok = false;
+        res.relres = relres_of(hRR, &ok);
+        res.refine = std::max(1, o.max_refine);
+        return res;
+    }
     if (o.precision == PGCP_FP64) {
         // FP64 PCG, restarted from the true residual while recursion drift
         // leaves it above the tolerance

@@ -7,7 +7,7 @@
         and reported, not raised.
 `final` the whole pipeline at --n vertices (final solve included).
 
-Usage: python -m paper_1903_12359_gb300.profile_cases dncp --n 1000000 --max-iters 300
+Usage: python -m paper_1903_12359_gb300.profile_cases dncp --n 1000000 --max-iters 300 [--local-precision 0|2]
 """
 import argparse
 import json
@@ -20,6 +20,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--max-iters", type=int, default=300)
+    ap.add_argument("--local-precision", type=int, default=2, help="0 FP64 PCG, 2 double-float PCG")
     a = ap.parse_args(argv)
     import torch
     from paper_1903_12359_gb300 import api, build, meshgen
@@ -30,7 +31,7 @@ def main(argv=None):
     L = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
     if a.case == "dncp":
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, max_iters=a.max_iters,
-                          max_refine=1)
+                          max_refine=1, local_precision=a.local_precision)
         part = ctx.partition(V, F, face_labels=L)
         try:
             part.local_param()
@@ -45,7 +46,8 @@ def main(argv=None):
                           "pcg_ms": st["pcg_ms"], "pcg_bytes": st["pcg_bytes"],
                           "pcg_launches": st["pcg_launches"]}))
     else:
-        ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10)
+        ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10,
+                          local_precision=a.local_precision)
         part = ctx.partition(V, F, face_labels=L)
         part.local_param()
         part.weld()

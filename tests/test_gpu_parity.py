@@ -97,10 +97,13 @@ def test_csr_pattern_bit_exact_values_close(api, name):
 
 
 @pytest.mark.parametrize("name", CASES)
-def test_dncp_fp64_matches_direct_solve(api, name):
+@pytest.mark.parametrize("local_precision", [0, 2], ids=["fp64", "df64"])
+def test_dncp_matches_direct_solve(api, name, local_precision):
+    """FP64 PCG, and double-float PCG inside FP64 refinement: 1e-9 absolute."""
     m, variant = _case(name)
-    ctx, part = _gpu_part(api, m, variant)
+    ctx, part = _gpu_part(api, m, variant, local_precision=local_precision)
     part.local_param()
+    assert part.get_stats()["dncp_relres"] <= 1e-13
     u = part.coords(0).cpu().numpy()
     P = o_partition(m.V, m.F, face_labels=m.face_labels)
     voff = np.concatenate([[0], np.cumsum([v.size for v in P.verts])])
@@ -138,10 +141,11 @@ def test_weld_on_identical_inputs(api, name):
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-8)])
-def test_final_coordinates_match_oracle(api, name, precision, tol):
+@pytest.mark.parametrize("precision,local_precision,tol", [(0, 0, 1e-9), (1, 0, 1e-8), (2, 2, 1e-9), (1, 2, 1e-8)],
+                         ids=["fp64", "fp32ref", "df64", "df64+fp32ref"])
+def test_final_coordinates_match_oracle(api, name, precision, local_precision, tol):
     m, variant = _case(name)
-    ctx, part = _gpu_part(api, m, variant, precision=precision, tol=1e-13)
+    ctx, part = _gpu_part(api, m, variant, precision=precision, tol=1e-13, local_precision=local_precision)
     part.local_param()
     part.weld()
     out = part.global_solve().cpu().numpy()
