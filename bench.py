@@ -313,10 +313,10 @@ def main():
     dncp_iters = sum(s["dncp_iters"] for s in stats)
     achieved = pcg_bytes / (pcg_ms / 1000.0) / 1e9 if pcg_ms > 0 else 0.0
     df = args.local_precision == 2
-    kname = "k_pcg_df" if df else "k_pcg<double,1>"
+    kname = "k_pcg_run<ArithDF>" if df else "k_pcg<double,1>"
     tr = ncu_traffic(kname, os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg_df.cu" if df else "pcg.cu"))
     peak = hbm if hbm else 6800.0
-    kdesc = ("k_pcg_df (persistent batched double-float PCG in FP64 refinement, local DNCP solves)" if df
+    kdesc = ("k_pcg_run<ArithDF> (persistent batched double-float PCG in FP64 refinement, local DNCP solves)" if df
              else "k_pcg<double,1> (persistent batched FP64 PCG, local DNCP solves)")
     roofline = {"kernel": kdesc, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -63,9 +63,11 @@ typedef struct {
     int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
     int32_t local_precision;  /* pgcp_precision of the DNCP solve (FP32_REFINED stalls: with two pins
                                  its conditioning is beyond FP32 refinement) */
-    int32_t spmv_lanes;       /* threads per matrix row in the PCG SpMV: 1, 2, 4 or 8 (autotuner output;
-                                 0 = default 1) */
-    int32_t reserved[5];
+    int32_t spmv_lanes;       /* threads per matrix row in the FP64 PCG SpMV: 1, 2, 4 or 8 (autotuner
+                                 output; 0 = default 1) */
+    int32_t pcg_blocks_per_sm;/* resident 256-thread blocks per SM of the mixed-precision PCG kernel:
+                                 3 (more registers) or 4 (more warps); autotuner output, 0 = default 4 */
+    int32_t reserved[4];
 } pgcp_options;
 
 /* Per-call statistics (host struct, filled by pgcp_global_solve). */

@@ -23,10 +23,11 @@
 // its tiles are then skipped.  Scalar accumulators rotate over 3 slots, so no
 // extra syncs are needed to reset them.
 //
-// Precision: FP64, or FP32 inner solves (FP32 SpMV and vectors, per-thread
-// FP32 partial sums reduced in FP64) inside FP64 iterative refinement:
-// r64 = -A64 x64 is computed in FP64 from FP64 matrix values, the FP32 solve
-// returns a correction, x64 += d.
+// This file holds the FP64 path (one kernel for the whole solve) and the
+// solver driver.  The mixed-precision paths (FP32 or double-float inner solves
+// inside FP64 iterative refinement: r64 = -A64 x64 computed in FP64 from FP64
+// matrix values, the inner solve returns a correction, x64 += d) run the
+// run-based kernel of pcg_df.cu.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -424,26 +425,6 @@ __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __rest
                RZ ? &RZ[2 * s] : nullptr, RZ ? &RZ[2 * s + 1] : nullptr);
 }
 
-// <b, b> and <b, D^-1 b> of an FP32 right-hand side, per (piece, coordinate).
-__global__ void k_rhs_stats(const Tile* __restrict__ tiles, const float* __restrict__ dinv,
-                            const float2* __restrict__ b, double* __restrict__ RR, double* __restrict__ RZ,
-                            float2* __restrict__ z) {
-    const Tile t = tiles[blockIdx.x];
-    float a0 = 0, a1 = 0, z0 = 0, z1 = 0;
-    for (int i = t.lo + threadIdx.x; i < t.hi; i += blockDim.x) {
-        const float di = dinv[i];
-        const float2 v = b[i];
-        z[i] = make_float2(di * v.x, di * v.y);
-        if (di == 0.f) continue;
-        a0 += v.x * v.x;
-        a1 += v.y * v.y;
-        z0 += v.x * (di * v.x);
-        z1 += v.y * (di * v.y);
-    }
-    const int s = t.seg;
-    block_add4(a0, a1, z0, z1, &RR[2 * s], &RR[2 * s + 1], &RZ[2 * s], &RZ[2 * s + 1]);
-}
-
 __global__ void k_tile_stats(Tile* tiles, const int32_t* __restrict__ rp, const uint8_t* __restrict__ fixed) {
     Tile& t = tiles[blockIdx.x];
     int fr = 0, fz = 0;
@@ -481,24 +462,6 @@ __global__ void k_dinv(int64_t n, const double* __restrict__ diag, const uint8_t
     double d = fixed[i] ? 0.0 : 1.0 / diag[i];
     d64[i] = d;
     d32[i] = (float)d;
-}
-
-__global__ void k_to_f32(int64_t n, const double2* __restrict__ a, float2* __restrict__ b, float2* __restrict__ zero1,
-                         float2* __restrict__ zero2, float2* __restrict__ zero3) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    b[i] = make_float2((float)a[i].x, (float)a[i].y);
-    zero1[i] = make_float2(0.f, 0.f);
-    zero2[i] = make_float2(0.f, 0.f);
-    zero3[i] = make_float2(0.f, 0.f);
-}
-
-__global__ void k_add_correction(int64_t n, const double* __restrict__ dinv64, const float2* __restrict__ d,
-                                 double2* __restrict__ x) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || dinv64[i] == 0.0) return;
-    x[i].x += (double)d[i].x;
-    x[i].y += (double)d[i].y;
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
@@ -621,10 +584,12 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     };
     DBuf<double2> r64;
     r64.alloc(n, s);
-    if (o.precision == PGCP_DF64_REFINED) {
-        // double-float inner solves to the final tolerance, FP64 residual outside
+    if (o.precision == PGCP_DF64_REFINED || o.precision == PGCP_FP32_REFINED) {
+        // run-based inner solves (double-float or FP32), FP64 residual outside
+        const int f32 = o.precision == PGCP_FP32_REFINED;
+        const double itol2 = o.inner_tol * o.inner_tol;
         DfSystem D;
-        df_build(ctx, P, dncp, fixed, D);
+        df_build(ctx, P, dncp, fixed, f32, D);
         for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
             RRo.zero();
             { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
@@ -635,13 +600,17 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
             res.relres = relres_of(hRR, &ok);
             res.refine = outer;
             if (ok) return res;
+            // thresholds on the inner residual: the final tolerance (double-float),
+            // or a fixed reduction of this right-hand side (FP32); converged
+            // pieces (coordinates) are frozen
             for (int i = 0; i < S; ++i) {
                 for (int c = 0; c < 2; ++c) {
                     const int j = 2 * i + c;
                     bool conv;
                     if (dncp) conv = hRR[2 * i] + hRR[2 * i + 1] <= tol2 * (hBB[2 * i] + hBB[2 * i + 1]);
                     else conv = hRR[j] <= tol2 * hBB[j];
-                    hTHR[j] = conv ? INFINITY : 0.25 * tol2 * hBB[j];
+                    hTHR[j] = conv ? INFINITY
+                                   : (f32 ? std::max(itol2 * hRR[j], 0.25 * tol2 * hBB[j]) : 0.25 * tol2 * hBB[j]);
                 }
             }
             res.iters += df_solve(ctx, P, D, r64.p, x, hTHR, o.max_iters);
@@ -700,62 +669,7 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         res.refine = std::max(1, o.max_refine);
         return res;
     }
-    // ---- FP32 inner solves inside FP64 refinement
-    DBuf<float2> b32, d32, p32, q32, z32;
-    z32.alloc(n, s);
-    b32.alloc(n, s);
-    d32.alloc(n, s);
-    p32.alloc(n, s);
-    q32.alloc(n, s);
-    const double itol2 = o.inner_tol * o.inner_tol;
-    for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
-        RRo.zero();
-        { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                      P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr); ::pgcp::note_launch(); }
-        PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PGCP_CUDA(cudaStreamSynchronize(s));
-        bool ok = false;
-        res.relres = relres_of(hRR, &ok);
-        res.refine = outer;
-        if (ok) return res;
-        // inner solve on A32 d = r64: thresholds relative to this right-hand side;
-        // pieces (coordinates) already converged are frozen
-        for (int i = 0; i < S; ++i) {
-            for (int c = 0; c < 2; ++c) {
-                int j = 2 * i + c;
-                bool conv;
-                if (dncp) conv = hRR[2 * i] + hRR[2 * i + 1] <= tol2 * (hBB[2 * i] + hBB[2 * i + 1]);
-                else conv = hRR[j] <= tol2 * hBB[j];
-                hTHR[j] = conv ? INFINITY : std::max(itol2 * hRR[j], 0.25 * tol2 * hBB[j]);
-            }
-        }
-        PGCP_CUDA(cudaMemcpyAsync(THR.p, hTHR.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
-        { k_to_f32<<<nblk(n), 256, 0, s>>>(n, r64.p, b32.p, d32.p, p32.p, q32.p); ::pgcp::note_launch(); }
-        RZ.zero();
-        RR.zero();
-        PQ.zero();
-        ACT.zero();
-        iters.zero();
-        // RZ0, RR0 of the FP32 right-hand side (x = 0 so r = b)
-        { k_rhs_stats<<<nt, 256, 0, s>>>(d_tiles.p, dinv32.p, b32.p, RR.p, RZ.p, z32.p); ::pgcp::note_launch(); }
-        PcgArgs<float> a{n, P.row_ptr.p, P.col.p, P.val32.p, dinv32.p, P.nb.p, d32.p, b32.p, p32.p, q32.p, z32.p,
-                         d_tiles.p, (int32_t)tiles.size(), S, RZ.p, RR.p, PQ.p, ACT.p, THR.p, iters.p, out_it.p,
-                         o.max_iters, dncp, o.spmv_lanes, work.p};
-        launch_pcg_lanes<float>(ctx, P, a);
-        int it = 0;
-        PGCP_CUDA(cudaMemcpyAsync(&it, out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        { k_add_correction<<<nblk(n), 256, 0, s>>>(n, dinv64.p, d32.p, x); ::pgcp::note_launch(); }
-        PGCP_CUDA(cudaStreamSynchronize(s));
-        res.iters += it;
-    }
-    RRo.zero();
-    { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
-                                                  dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
-    PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-    PGCP_CUDA(cudaStreamSynchronize(s));
-    bool ok = false;
-    res.relres = relres_of(hRR, &ok);
-    res.refine = std::max(1, o.max_refine);
+    fail(PGCP_E_ARG, "unknown solver precision " + std::to_string(o.precision));
     return res;
 }
 

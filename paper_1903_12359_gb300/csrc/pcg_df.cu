@@ -1,16 +1,18 @@
-// Double-float PCG for the batched local (DNCP) and Laplace systems, inside
-// FP64 iterative refinement (Sections 4.2 and 4.5 define the systems; the
-// solver is this library's).
+// Run-based persistent PCG for the batched local (DNCP) and Laplace systems,
+// inside FP64 iterative refinement (Sections 4.2 and 4.5 define the systems;
+// the solver is this library's).
 //
-// Why: the GB300 FP64 pipe issues 2 DFMA per SM per cycle against 128 FFMA,
-// and an FP64 Jacobi-PCG over these meshes is bound by it (14 DFMA per row in
-// the SpMV alone).  FP32 alone is too coarse for the DNCP system (Jacobi-
-// scaled condition number ~1e7: FP32 refinement stalls).  A double-float
-// number is an unevaluated sum hi + lo of two floats, about 48 significant
-// bits, computed with error-free transformations on the FP32 pipe:
-//   TwoSum (Knuth), Fast2Sum (Dekker) and the FMA-based TwoProduct
-//   (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005).
-// The __f*_rn intrinsics keep the compiler from contracting them.
+// Two arithmetics share one kernel template:
+// * double-float (ArithDF): a number is the unevaluated sum hi + lo of two
+//   floats, about 48 significant bits, computed with error-free
+//   transformations on the FP32 pipe -- TwoSum (Knuth), Fast2Sum (Dekker) and
+//   the FMA-based TwoProduct (Ogita, Rump and Oishi, "Accurate sum and dot
+//   product", 2005).  The __f*_rn intrinsics keep the compiler from
+//   contracting them.  GB300's FP64 pipe issues 2 DFMA per SM per cycle
+//   against 128 FFMA, and an FP64 PCG over these meshes is bound by it, while
+//   FP32 alone is too coarse for the DNCP system (its refinement stalls).
+// * FP32 (ArithF32): FP32 values and FP32 accumulation, for the Laplace solve.
+// The FP64 residual outside decides convergence in both.
 //
 // The system is solved in symmetrically Jacobi-scaled form,
 //   A~ = S A S,  S = diag(d)^-1/2,  A~ x~ = S r64,  x += S x~,
@@ -24,7 +26,7 @@
 // One persistent cooperative kernel runs all iterations.  Rows are split
 // evenly over the blocks; a block's range is cut at piece boundaries into
 // "runs", and scalars and reductions are per run (one block reduction per
-// run and phase).  Per iteration:
+// run and phase, on the FP32 pipe in double-float).  Per iteration:
 //   phase B: beta = rr_k / rr_{k-1}; p = r + beta p; q = A~ r + beta q; <p, q>
 //   grid sync
 //   phase A: alpha = rr_k / <p, q>; x~ += alpha p; r -= alpha q;
@@ -73,6 +75,11 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {
     return fast_two_sum(s.x, t);
 }
 
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, b.x);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+
 __device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
 
 __device__ __forceinline__ float2 d_to_df(double d) {
@@ -80,25 +87,61 @@ __device__ __forceinline__ float2 d_to_df(double d) {
     return make_float2(h, __double2float_rn(d - (double)h));
 }
 
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// Arithmetic policies: one scalar S (also the stored matrix value) and a
+// row's (x, y) pair V.
+// ArithDF: double-float scalars, V = float4 {x.hi, x.lo, y.hi, y.lo}.
+// ArithF32: FP32 scalars, V = float2, FP32 accumulation.
+struct ArithDF {
+    using S = float2;
+    using V = float4;
+    static constexpr int bytes = 8;
+    static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ S fma(S acc, S a, S b) { return df_fma(acc, a, b); }
+    static __device__ __forceinline__ S neg(S a) { return make_float2(-a.x, -a.y); }
+    static __device__ __forceinline__ S cx(V v) { return make_float2(v.x, v.y); }
+    static __device__ __forceinline__ S cy(V v) { return make_float2(v.z, v.w); }
+    static __device__ __forceinline__ V pack(S a, S b) { return make_float4(a.x, a.y, b.x, b.y); }
+    static __device__ __forceinline__ V vzero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ S from_d(double d) { return d_to_df(d); }
+    static __device__ __forceinline__ double to_d(S a) { return df_to_d(a); }
+    static __device__ __forceinline__ float2 as_df(S a) { return a; }
+    static __device__ __forceinline__ float lead(S a) { return a.x; }
+};
+struct ArithF32 {
+    using S = float;
+    using V = float2;
+    static constexpr int bytes = 4;
+    static __device__ __forceinline__ S zero() { return 0.f; }
+    static __device__ __forceinline__ S fma(S acc, S a, S b) { return fmaf(a, b, acc); }
+    static __device__ __forceinline__ S neg(S a) { return -a; }
+    static __device__ __forceinline__ S cx(V v) { return v.x; }
+    static __device__ __forceinline__ S cy(V v) { return v.y; }
+    static __device__ __forceinline__ V pack(S a, S b) { return make_float2(a, b); }
+    static __device__ __forceinline__ V vzero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ S from_d(double d) { return __double2float_rn(d); }
+    static __device__ __forceinline__ double to_d(S a) { return (double)a; }
+    static __device__ __forceinline__ float2 as_df(S a) { return make_float2(a, 0.f); }
+    static __device__ __forceinline__ float lead(S a) { return a; }
+};
 
-constexpr int DF_THREADS = 256;
+constexpr int RUN_THREADS = 256;
+// Resident blocks per SM the kernel is compiled for (MINB): 4 caps it at 64
+// registers (32 warps per SM), 3 at 80 (24 warps, no spills in double-float).
 
-struct DfArgs {
+template <typename A>
+struct RunArgs {
     int32_t n;
     int32_t nseg;
     const int32_t* __restrict__ rp;
-    const int32_t* __restrict__ col;    // ~c marks a cross (area-term) entry
-    const float2* __restrict__ val;     // scaled values, double-float
-    const float* __restrict__ dgn;      // diagonal of A (0 at fixed rows), for the unscaled norm
-    float4* x;   // x~ (x, y components, double-float each)
-    float4* r;
-    float4* p;
-    float4* q;
+    const int32_t* __restrict__ col;        // ~c marks a cross (area-term) entry
+    const typename A::S* __restrict__ val;  // scaled values
+    const float* __restrict__ dgn;          // diagonal of A (0 at fixed rows), for the unscaled norm
+    typename A::V* x;   // x~
+    typename A::V* r;
+    typename A::V* p;
+    typename A::V* q;
     const DfRun* __restrict__ runs;
-    const int32_t* __restrict__ run_off;   // [grid + 1]
+    const int32_t* __restrict__ run_off;    // [grid + 1]
     double* RR;    // [3][2 nseg] scaled <r, r>
     double* RD;    // [3][2 nseg] unscaled sum d r^2
     double* PQ;    // [2][2 nseg]
@@ -115,46 +158,73 @@ __device__ __forceinline__ bool piece_done(const double* RD, const double* THR, 
     return RD[2 * s + c] <= THR[2 * s + c];
 }
 
-// Sum NV doubles over the block; thread 0 gets the totals.
+// Sum NV double-float values over the block on the FP32 pipe; thread 0 gets
+// the totals as doubles.  red: NV * (warps) float2 of shared memory.
 template <int NV>
-__device__ __forceinline__ void block_sum(double* v, double* red) {
+__device__ __forceinline__ void block_sum_df(float2* v, float2* red, double* out) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        for (int i = 0; i < NV; ++i) {
+            float2 t;
+            t.x = __shfl_xor_sync(0xffffffffu, v[i].x, o);
+            t.y = __shfl_xor_sync(0xffffffffu, v[i].y, o);
+            v[i] = df_add(v[i], t);
+        }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
+    constexpr int NW = RUN_THREADS / 32;
+    __syncthreads();   // red is free (its previous readers are done)
     if (lane == 0)
 #pragma unroll
         for (int i = 0; i < NV; ++i) red[NV * warp + i] = v[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NV; ++i) v[i] = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    if (warp == 0) {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) v[i] += red[NV * w + i];
+        for (int i = 0; i < NV; ++i) {
+            float2 t = lane < NW ? red[NV * lane + i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = NW / 2; o > 0; o >>= 1) {
+                float2 u;
+                u.x = __shfl_xor_sync(0xffffffffu, t.x, o);
+                u.y = __shfl_xor_sync(0xffffffffu, t.y, o);
+                t = df_add(t, u);
+            }
+            if (lane == 0) out[i] = df_to_d(t);
+        }
     }
 }
 
-// One stored entry of the SpMV: w += v * r_c (or the cross form).
-__device__ __forceinline__ void spmv_entry(int32_t c, float2 v, const float4* __restrict__ r, float2& w0,
-                                           float2& w1) {
-    const bool cross = c < 0;
-    const float4 rc = r[cross ? ~c : c];
-    const float2 a0 = cross ? hi2(rc) : lo2(rc);
-    const float2 a1 = cross ? lo2(rc) : hi2(rc);
-    const float2 v0 = cross ? make_float2(-v.x, -v.y) : v;
-    w0 = df_fma(w0, v0, a0);
-    w1 = df_fma(w1, v, a1);
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
-__global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
+// One stored entry of the SpMV: w += v * r_c (or the cross form).
+template <typename A>
+__device__ __forceinline__ void spmv_entry(int32_t c, typename A::S v, const typename A::V* r, typename A::S& w0,
+                                           typename A::S& w1) {
+    const bool cross = c < 0;
+    const typename A::V rc = r[cross ? ~c : c];
+    const typename A::S a0 = cross ? A::cy(rc) : A::cx(rc);
+    const typename A::S a1 = cross ? A::cx(rc) : A::cy(rc);
+    const typename A::S v0 = cross ? A::neg(v) : v;
+    w0 = A::fma(w0, v0, a0);
+    w1 = A::fma(w1, v, a1);
+}
+
+template <typename A, int MINB>
+__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
+    using S = typename A::S;
+    using V = typename A::V;
     cg::grid_group grid = cg::this_grid();
-    __shared__ double red[4 * (DF_THREADS / 32)];
+    __shared__ float2 red[4 * (RUN_THREADS / 32)];
     __shared__ double sc[2][2];
     __shared__ int sflag[2][2];
     const int nseg = a.nseg;
     const int rb = a.run_off[blockIdx.x], re = a.run_off[blockIdx.x + 1];
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ colp = a.col;
+    const S* __restrict__ valp = a.val;
+    const float* __restrict__ dgp = a.dgn;
     unsigned long long wrows = 0, wnnz = 0;
     int k = 0;
     for (; k < a.max_iters; ++k) {
@@ -163,7 +233,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
         const double* RDk = a.RD + (k % 3) * 2 * nseg;
         double* PQk = a.PQ + (k % 2) * 2 * nseg;
         // ---------------- phase B: p = r + beta p, q = A~ r + beta q, <p, q>
-        if (blockIdx.x == 0) {
+        if (blockIdx.x == 0) {   // clear the slots phase A of this iteration fills
             double* z1 = a.RR + ((k + 1) % 3) * 2 * nseg;
             double* z2 = a.RD + ((k + 1) % 3) * 2 * nseg;
             for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) {
@@ -193,47 +263,70 @@ __global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
                 sflag[slot][0] = d0;
                 sflag[slot][1] = d1;
             }
-            __syncthreads();
+            __syncthreads();   // scalars of this run (double-buffered by run parity)
             const bool d0 = sflag[slot][0], d1 = sflag[slot][1];
             if (d0 && d1) continue;
             any = true;
-            const float2 beta0 = d_to_df(sc[slot][0]), beta1 = d_to_df(sc[slot][1]);
-            float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-            for (int row = run.lo + threadIdx.x; row < run.hi; row += blockDim.x) {
-                const int b = a.rp[row], e = a.rp[row + 1];
+            const S beta0 = A::from_d(sc[slot][0]), beta1 = A::from_d(sc[slot][1]);
+            S acc0 = A::zero(), acc1 = A::zero();
+            // software pipeline over this thread's rows: the next row's bounds are
+            // loaded, and its vectors and matrix slice prefetched into L2, before
+            // the current row's SpMV (prefetches hold no registers)
+            int row = run.lo + threadIdx.x;
+            int bn = 0, en = 0;
+            if (row < run.hi) {
+                bn = __ldg(rp + row);
+                en = __ldg(rp + row + 1);
+            }
+            for (; row < run.hi; row += blockDim.x) {
+                const int b = bn, e = en;
+                const int nxt = row + blockDim.x;
+                if (nxt < run.hi) {
+                    bn = __ldg(rp + nxt);
+                    en = __ldg(rp + nxt + 1);
+                    if (en > bn) {
+                        prefetch_l2(colp + bn);
+                        prefetch_l2(valp + bn);
+                        prefetch_l2(valp + en - 1);
+                        prefetch_l2(a.p + nxt);
+                        prefetch_l2(a.q + nxt);
+                        prefetch_l2(a.r + nxt);
+                    }
+                }
                 if (b == e) continue;   // fixed row
-                float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+                S w0 = A::zero(), w1 = A::zero();
                 int j = b;
                 for (; j + 4 <= e; j += 4) {
                     int32_t c[4];
-                    float2 v[4];
+                    S v[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        c[u] = a.col[j + u];
-                        v[u] = a.val[j + u];
+                        c[u] = __ldg(colp + j + u);
+                        v[u] = __ldg(valp + j + u);
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) spmv_entry(c[u], v[u], a.r, w0, w1);
+                    for (int u = 0; u < 4; ++u) spmv_entry<A>(c[u], v[u], a.r, w0, w1);
                 }
-                for (; j < e; ++j) spmv_entry(a.col[j], a.val[j], a.r, w0, w1);
-                const float4 rr = a.r[row];
-                float4 pp = a.p[row], qq = a.q[row];
-                float2 px = lo2(pp), py = hi2(pp), qx = lo2(qq), qy = hi2(qq);
+                for (; j < e; ++j) spmv_entry<A>(__ldg(colp + j), __ldg(valp + j), a.r, w0, w1);
+                const V rr = a.r[row];
+                const V pp = a.p[row], qq = a.q[row];
+                S px = A::cx(pp), py = A::cy(pp), qx = A::cx(qq), qy = A::cy(qq);
                 if (!d0) {
-                    px = df_fma(lo2(rr), beta0, px);
-                    qx = df_fma(w0, beta0, qx);
-                    acc0 = df_fma(acc0, px, qx);
+                    px = A::fma(A::cx(rr), beta0, px);
+                    qx = A::fma(w0, beta0, qx);
+                    acc0 = A::fma(acc0, px, qx);
                 }
                 if (!d1) {
-                    py = df_fma(hi2(rr), beta1, py);
-                    qy = df_fma(w1, beta1, qy);
-                    acc1 = df_fma(acc1, py, qy);
+                    py = A::fma(A::cy(rr), beta1, py);
+                    qy = A::fma(w1, beta1, qy);
+                    acc1 = A::fma(acc1, py, qy);
                 }
-                a.p[row] = pack(px, py);
-                a.q[row] = pack(qx, qy);
+                a.p[row] = A::pack(px, py);
+                a.q[row] = A::pack(qx, qy);
             }
-            double v[2] = {df_to_d(acc0), df_to_d(acc1)};
-            block_sum<2>(v, red);
+            float2 pv[2] = {A::as_df(acc0), A::as_df(acc1)};
+            double v[2];
+            block_sum_df<2>(pv, red, v);
             if (threadIdx.x == 0) {
                 atomicAdd(&PQk[2 * s], v[0]);
                 atomicAdd(&PQk[2 * s + 1], v[1]);
@@ -244,7 +337,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
         if (threadIdx.x == 0 && any) *(volatile unsigned*)&a.ACT[k % 3] = 1u;
         grid.sync();
         // ---------------- phase A: x~ += alpha p, r -= alpha q, norms
-        if (blockIdx.x == 0) {
+        if (blockIdx.x == 0) {   // clear the slots phase B of the next iteration fills
             double* z = a.PQ + ((k + 1) % 2) * 2 * nseg;
             for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) z[i] = 0.0;
             if (threadIdx.x == 0) a.ACT[(k + 1) % 3] = 0;
@@ -271,26 +364,35 @@ __global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
             }
             __syncthreads();
             if (sflag[slot][0]) continue;
-            const float2 al0 = d_to_df(sc[slot][0]), al1 = d_to_df(sc[slot][1]);
-            const float2 nal0 = make_float2(-al0.x, -al0.y), nal1 = make_float2(-al1.x, -al1.y);
-            float2 rr0 = make_float2(0.f, 0.f), rr1 = make_float2(0.f, 0.f);
+            const S al0 = A::from_d(sc[slot][0]), al1 = A::from_d(sc[slot][1]);
+            const S nal0 = A::neg(al0), nal1 = A::neg(al1);
+            S rr0 = A::zero(), rr1 = A::zero();
             float rd0 = 0.f, rd1 = 0.f;
             for (int row = run.lo + threadIdx.x; row < run.hi; row += blockDim.x) {
-                const float d = a.dgn[row];
+                const int nxt = row + blockDim.x;
+                if (nxt < run.hi) {   // next row's streams into L2 (no registers held)
+                    prefetch_l2(a.x + nxt);
+                    prefetch_l2(a.r + nxt);
+                    prefetch_l2(a.p + nxt);
+                    prefetch_l2(a.q + nxt);
+                }
+                const float d = __ldg(dgp + row);
                 if (d == 0.f) continue;   // fixed row
-                float4 xx = a.x[row], rv = a.r[row];
-                const float4 pp = a.p[row], qq = a.q[row];
-                const float2 x0 = df_fma(lo2(xx), al0, lo2(pp)), x1 = df_fma(hi2(xx), al1, hi2(pp));
-                const float2 r0 = df_fma(lo2(rv), nal0, lo2(qq)), r1 = df_fma(hi2(rv), nal1, hi2(qq));
-                a.x[row] = pack(x0, x1);
-                a.r[row] = pack(r0, r1);
-                rr0 = df_fma(rr0, r0, r0);
-                rr1 = df_fma(rr1, r1, r1);
-                rd0 = fmaf(d * r0.x, r0.x, rd0);
-                rd1 = fmaf(d * r1.x, r1.x, rd1);
+                const V xx = a.x[row], rv = a.r[row];
+                const V pp = a.p[row], qq = a.q[row];
+                const S x0 = A::fma(A::cx(xx), al0, A::cx(pp)), x1 = A::fma(A::cy(xx), al1, A::cy(pp));
+                const S r0 = A::fma(A::cx(rv), nal0, A::cx(qq)), r1 = A::fma(A::cy(rv), nal1, A::cy(qq));
+                a.x[row] = A::pack(x0, x1);
+                a.r[row] = A::pack(r0, r1);
+                rr0 = A::fma(rr0, r0, r0);
+                rr1 = A::fma(rr1, r1, r1);
+                const float l0 = A::lead(r0), l1 = A::lead(r1);
+                rd0 = fmaf(d * l0, l0, rd0);
+                rd1 = fmaf(d * l1, l1, rd1);
             }
-            double v[4] = {df_to_d(rr0), df_to_d(rr1), (double)rd0, (double)rd1};
-            block_sum<4>(v, red);
+            float2 pv[4] = {A::as_df(rr0), A::as_df(rr1), make_float2(rd0, 0.f), make_float2(rd1, 0.f)};
+            double v[4];
+            block_sum_df<4>(pv, red, v);
             if (threadIdx.x == 0) {
                 atomicAdd(&RRn[2 * s], v[0]);
                 atomicAdd(&RRn[2 * s + 1], v[1]);
@@ -312,9 +414,9 @@ __global__ void __launch_bounds__(DF_THREADS) k_pcg_df(DfArgs a) {
 
 // Stored entries of row i of A~: free columns of a free row, plus the DNCP
 // cross entries to free loop neighbours.
-__global__ void k_df_count(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           const uint8_t* __restrict__ fixed, const int2* __restrict__ nb, int dncp,
-                           int32_t* __restrict__ cnt) {
+__global__ void k_run_count(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const uint8_t* __restrict__ fixed, const int2* __restrict__ nb, int dncp,
+                            int32_t* __restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = 0;
@@ -328,12 +430,13 @@ __global__ void k_df_count(int64_t n, const int32_t* __restrict__ rp, const int3
     cnt[i] = c;
 }
 
-__global__ void k_df_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const double* __restrict__ val, const double* __restrict__ diag,
-                          const uint8_t* __restrict__ fixed, const int2* __restrict__ nb, int dncp,
-                          const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
-                          int32_t* __restrict__ rp2, int32_t* __restrict__ col2,
-                          float2* __restrict__ val2, double* __restrict__ sc, float* __restrict__ dgn) {
+template <typename A>
+__global__ void k_run_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ diag,
+                           const uint8_t* __restrict__ fixed, const int2* __restrict__ nb, int dncp,
+                           const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                           int32_t* __restrict__ rp2, int32_t* __restrict__ col2, typename A::S* __restrict__ val2,
+                           double* __restrict__ sc, float* __restrict__ dgn) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t o = off[i];
@@ -352,7 +455,7 @@ __global__ void k_df_fill(int64_t n, const int32_t* __restrict__ rp, const int32
         const int c = col[j];
         if (fixed[c]) continue;
         col2[t] = c;
-        val2[t] = d_to_df(val[j] * si / sqrt(diag[c]));
+        val2[t] = A::from_d(val[j] * si / sqrt(diag[c]));
         ++t;
     }
     if (dncp) {
@@ -360,12 +463,12 @@ __global__ void k_df_fill(int64_t n, const int32_t* __restrict__ rp, const int32
         if (pn.x >= 0) {
             if (!fixed[pn.x]) {
                 col2[t] = ~pn.x;
-                val2[t] = d_to_df(-0.5 * si / sqrt(diag[pn.x]));
+                val2[t] = A::from_d(-0.5 * si / sqrt(diag[pn.x]));
                 ++t;
             }
             if (!fixed[pn.y]) {
                 col2[t] = ~pn.y;
-                val2[t] = d_to_df(0.5 * si / sqrt(diag[pn.y]));
+                val2[t] = A::from_d(0.5 * si / sqrt(diag[pn.y]));
                 ++t;
             }
         }
@@ -373,7 +476,7 @@ __global__ void k_df_fill(int64_t n, const int32_t* __restrict__ rp, const int32
 }
 
 // frows / fnnz per run (one block per run)
-__global__ void k_df_run_stats(DfRun* runs, const int32_t* __restrict__ rp2) {
+__global__ void k_run_stats(DfRun* runs, const int32_t* __restrict__ rp2) {
     DfRun& r = runs[blockIdx.x];
     int fr = 0;
     for (int i = r.lo + threadIdx.x; i < r.hi; i += blockDim.x) fr += rp2[i + 1] > rp2[i] ? 1 : 0;
@@ -389,12 +492,34 @@ __global__ void k_df_run_stats(DfRun* runs, const int32_t* __restrict__ rp2) {
     }
 }
 
-// r~ = S r64 (0 at fixed rows), x~ = p = q = 0, and slot-0 norms per run.
-__global__ void k_df_prep(const DfRun* __restrict__ runs, const int32_t* __restrict__ run_off,
-                          const double2* __restrict__ r64, const double* __restrict__ sc, float4* __restrict__ x,
-                          float4* __restrict__ r, float4* __restrict__ p, float4* __restrict__ q,
-                          double* __restrict__ RR, double* __restrict__ RD) {
-    __shared__ double red[4 * (DF_THREADS / 32)];
+// Sum NV doubles over the block (set-up kernels only); thread 0 gets the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum64(double* v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[NV * warp + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NV; ++i) v[i] = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] += red[NV * w + i];
+    }
+}
+
+// r~ = S r64 (0 at fixed rows), x~ = p = q = 0, and the slot-0 norms per run.
+template <typename A>
+__global__ void k_run_prep(const DfRun* __restrict__ runs, const int32_t* __restrict__ run_off,
+                           const double2* __restrict__ r64, const double* __restrict__ sc, typename A::V* __restrict__ x,
+                           typename A::V* __restrict__ r, typename A::V* __restrict__ p, typename A::V* __restrict__ q,
+                           double* __restrict__ RR, double* __restrict__ RD) {
+    __shared__ double red[4 * (RUN_THREADS / 32)];
     for (int ri = run_off[blockIdx.x]; ri < run_off[blockIdx.x + 1]; ++ri) {
         const DfRun run = runs[ri];
         double v[4] = {0, 0, 0, 0};
@@ -402,20 +527,21 @@ __global__ void k_df_prep(const DfRun* __restrict__ runs, const int32_t* __restr
             const double si = sc[i];
             const double2 ri64 = r64[i];
             const double a0 = si * ri64.x, a1 = si * ri64.y;
-            const float2 f0 = d_to_df(a0), f1 = d_to_df(a1);
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            x[i] = z;
-            p[i] = z;
-            q[i] = z;
-            r[i] = pack(f0, f1);
+            const typename A::S f0 = A::from_d(a0), f1 = A::from_d(a1);
+            x[i] = A::vzero();
+            p[i] = A::vzero();
+            q[i] = A::vzero();
+            r[i] = A::pack(f0, f1);
             if (si != 0.0) {
-                v[0] += a0 * a0;
-                v[1] += a1 * a1;
+                // the stored (rounded) values, so CG starts from what it iterates on
+                const double g0 = A::to_d(f0), g1 = A::to_d(f1);
+                v[0] += g0 * g0;
+                v[1] += g1 * g1;
                 v[2] += ri64.x * ri64.x;
                 v[3] += ri64.y * ri64.y;
             }
         }
-        block_sum<4>(v, red);
+        block_sum64<4>(v, red);
         if (threadIdx.x == 0) {
             atomicAdd(&RR[2 * run.seg], v[0]);
             atomicAdd(&RR[2 * run.seg + 1], v[1]);
@@ -427,51 +553,100 @@ __global__ void k_df_prep(const DfRun* __restrict__ runs, const int32_t* __restr
 }
 
 // x += S x~ on free rows
-__global__ void k_df_finish(int64_t n, const double* __restrict__ sc, const float4* __restrict__ xs,
-                            double2* __restrict__ x) {
+template <typename A>
+__global__ void k_run_finish(int64_t n, const double* __restrict__ sc, const typename A::V* __restrict__ xs,
+                             double2* __restrict__ x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double si = sc[i];
     if (si == 0.0) return;
-    const float4 v = xs[i];
-    x[i].x += si * df_to_d(lo2(v));
-    x[i].y += si * df_to_d(hi2(v));
+    const typename A::V v = xs[i];
+    x[i].x += si * A::to_d(A::cx(v));
+    x[i].y += si * A::to_d(A::cy(v));
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
+
+template <typename A>
+void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSystem& D, const int32_t* cnt,
+                 const int64_t* off) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = D.n;
+    D.val.alloc(std::max<int64_t>(D.nnz, 1) * sizeof(typename A::S), s);
+    { k_run_fill<A><<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.diag64.p, fixed, P.nb.p, dncp, off,
+                                            cnt, D.rp.p, D.col.p, reinterpret_cast<typename A::S*>(D.val.p), D.sc.p,
+                                            D.dgn.p); ::pgcp::note_launch(); }
+    PGCP_CUDA(cudaGetLastError());
+    int per_sm = 0;
+    const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
+    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RUN_THREADS, 0));
+    if (per_sm <= 0) fail(PGCP_E_CUDA, "run-based PCG kernel cannot be resident");
+    D.per_sm = per_sm;
+    const size_t vb = sizeof(typename A::V);
+    D.x.alloc(n * vb, s);
+    D.r.alloc(n * vb, s);
+    D.p.alloc(n * vb, s);
+    D.q.alloc(n * vb, s);
+}
+
+template <typename A>
+void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int max_iters, cudaEvent_t e0) {
+    cudaStream_t s = ctx->stream;
+    using V = typename A::V;
+    V* xv = reinterpret_cast<V*>(D.x.p);
+    V* rv = reinterpret_cast<V*>(D.r.p);
+    V* pv = reinterpret_cast<V*>(D.p.p);
+    V* qv = reinterpret_cast<V*>(D.q.p);
+    { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, D.RR.p,
+                                                            D.RD.p); ::pgcp::note_launch(); }
+    PGCP_CUDA(cudaGetLastError());
+    PGCP_CUDA(cudaEventRecord(e0, s));
+    RunArgs<A> a{(int32_t)D.n, P.K, D.rp.p, D.col.p, reinterpret_cast<const typename A::S*>(D.val.p), D.dgn.p, xv, rv,
+                 pv, qv, D.runs.p, D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, max_iters,
+                 D.dncp, D.work.p};
+    void* args[] = {(void*)&a};
+    const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
+    { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(D.grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+}
+
+template <typename A>
+void finish_typed(pgcp_ctx* ctx, DfSystem& D, double2* x) {
+    { k_run_finish<A><<<nblk(D.n), 256, 0, ctx->stream>>>(D.n, D.sc.p, reinterpret_cast<const typename A::V*>(D.x.p),
+                                                          x); ::pgcp::note_launch(); }
+    PGCP_CUDA(cudaGetLastError());
+}
 
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 
-void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSystem& D) {
+void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D) {
     cudaStream_t s = ctx->stream;
     const int64_t n = P.Nc;
-    if (n >= INT32_MAX) fail(PGCP_E_ARG, "double-float PCG: too many rows");
+    if (n >= INT32_MAX) fail(PGCP_E_ARG, "run-based PCG: too many rows");
     D.n = n;
     D.dncp = dncp;
+    D.f32 = f32;
+    const int bps = ctx->opt.pcg_blocks_per_sm;
+    if (bps != 0 && bps != 3 && bps != 4) fail(PGCP_E_ARG, "pcg_blocks_per_sm must be 0, 3 or 4");
+    D.minb = bps == 3 ? 3 : 4;
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;
     cnt.alloc(n, s);
     off.alloc(n, s);
-    { k_df_count<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, fixed, P.nb.p, dncp, cnt.p); ::pgcp::note_launch(); }
+    { k_run_count<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, fixed, P.nb.p, dncp, cnt.p); ::pgcp::note_launch(); }
     int64_t nnz2 = 0;
     exclusive_scan_i32_to_i64(cnt.p, off.p, n, s, &nnz2);
-    if (nnz2 >= INT32_MAX) fail(PGCP_E_ARG, "double-float PCG: too many stored entries");
+    if (nnz2 >= INT32_MAX) fail(PGCP_E_ARG, "run-based PCG: too many stored entries");
     D.nnz = nnz2;
     D.rp.alloc(n + 1, s);
     D.col.alloc(std::max<int64_t>(nnz2, 1), s);
-    D.val.alloc(std::max<int64_t>(nnz2, 1), s);
     D.sc.alloc(n, s);
     D.dgn.alloc(n, s);
-    { k_df_fill<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.diag64.p, fixed, P.nb.p, dncp, off.p,
-                                       cnt.p, D.rp.p, D.col.p, D.val.p, D.sc.p, D.dgn.p); ::pgcp::note_launch(); }
-    PGCP_CUDA(cudaGetLastError());
-    // persistent grid and its row runs
-    int per_sm = 0;
-    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, DF_THREADS, 0));
-    if (per_sm <= 0) fail(PGCP_E_CUDA, "double-float PCG kernel cannot be resident");
-    int grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 32)));
+    if (f32) build_typed<ArithF32>(ctx, P, dncp, fixed, D, cnt.p, off.p);
+    else build_typed<ArithDF>(ctx, P, dncp, fixed, D, cnt.p, off.p);
+    // persistent grid (all co-resident blocks) and its row runs
+    int grid = (int)std::min<int64_t>((int64_t)D.per_sm * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 32)));
     grid = std::max(grid, 1);
     D.grid = grid;
     std::vector<DfRun> runs;
@@ -480,7 +655,6 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSystem& 
         int64_t lo = n * b / grid, hi = n * (b + 1) / grid;
         roff[b] = (int32_t)runs.size();
         while (lo < hi) {
-            // piece holding row lo
             const int seg = (int)(std::upper_bound(P.voff.begin(), P.voff.end(), lo) - P.voff.begin()) - 1;
             const int64_t end = std::min<int64_t>(hi, P.voff[seg + 1]);
             runs.push_back(DfRun{seg, (int32_t)lo, (int32_t)end, 0, 0, 0, 0, 0});
@@ -494,12 +668,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSystem& 
     PGCP_CUDA(cudaMemcpyAsync(D.runs.p, runs.data(), runs.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
     PGCP_CUDA(cudaMemcpyAsync(D.run_off.p, roff.data(), roff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (D.nruns > 0) {
-        { k_df_run_stats<<<(unsigned)D.nruns, 256, 0, s>>>(D.runs.p, D.rp.p); ::pgcp::note_launch(); }
+        { k_run_stats<<<(unsigned)D.nruns, 256, 0, s>>>(D.runs.p, D.rp.p); ::pgcp::note_launch(); }
     }
-    D.x.alloc(n, s);
-    D.r.alloc(n, s);
-    D.p.alloc(n, s);
-    D.q.alloc(n, s);
     const int S = P.K;
     D.RR.alloc(3 * 2 * S, s);
     D.RD.alloc(3 * 2 * S, s);
@@ -521,21 +691,16 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     D.PQ.zero();
     D.ACT.zero();
     PGCP_CUDA(cudaMemcpyAsync(D.THR.p, thr.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
-    { k_df_prep<<<(unsigned)D.grid, DF_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, D.x.p, D.r.p, D.p.p,
-                                                        D.q.p, D.RR.p, D.RD.p); ::pgcp::note_launch(); }
-    PGCP_CUDA(cudaGetLastError());
-    DfArgs a{(int32_t)D.n, S, D.rp.p, D.col.p, D.val.p, D.dgn.p, D.x.p, D.r.p, D.p.p, D.q.p, D.runs.p,
-             D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, max_iters, D.dncp, D.work.p};
+    PGCP_CUDA(cudaMemsetAsync(D.work.p, 0, 2 * sizeof(unsigned long long), s));
     cudaEvent_t e0, e1;
     PGCP_CUDA(cudaEventCreate(&e0));
     PGCP_CUDA(cudaEventCreate(&e1));
-    PGCP_CUDA(cudaMemsetAsync(D.work.p, 0, 2 * sizeof(unsigned long long), s));
-    PGCP_CUDA(cudaEventRecord(e0, s));
-    void* args[] = {(void*)&a};
-    { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_pcg_df, dim3(D.grid), dim3(DF_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    // the event pair brackets the persistent kernel only (e0 follows the prep kernel)
+    if (D.f32) solve_typed<ArithF32>(ctx, P, D, r64, max_iters, e0);
+    else solve_typed<ArithDF>(ctx, P, D, r64, max_iters, e0);
     PGCP_CUDA(cudaEventRecord(e1, s));
-    { k_df_finish<<<nblk(D.n), 256, 0, s>>>(D.n, D.sc.p, D.x.p, x); ::pgcp::note_launch(); }
-    PGCP_CUDA(cudaGetLastError());
+    if (D.f32) finish_typed<ArithF32>(ctx, D, x);
+    else finish_typed<ArithDF>(ctx, D, x);
     unsigned long long w[2] = {0, 0};
     int it = 0;
     PGCP_CUDA(cudaMemcpyAsync(w, D.work.p, sizeof(w), cudaMemcpyDeviceToHost, s));
@@ -546,10 +711,12 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     P.stats.pcg_ms += ms;
-    // per free row and iteration: phase B row pointer 4, r 16, p r/w 32, q r/w 32;
-    // phase A diagonal 4, x r/w 32, r r/w 32, p 16, q 16 -> 184 B;
-    // per stored entry: column 4 + double-float value 8 (gathered r hits cache)
-    P.stats.pcg_bytes += (double)w[0] * 184.0 + (double)w[1] * 12.0;
+    // Per free row and iteration, with vector pairs of 2T bytes (T = 8 for
+    // double-float, 4 for FP32): phase B row pointer 4, r 2T, p r/w 4T,
+    // q r/w 4T; phase A diagonal 4, x r/w 4T, r r/w 4T, p 2T, q 2T
+    // -> 8 + 22T.  Per stored entry: column 4 + value T (gathered r hits cache).
+    const double T = D.f32 ? 4.0 : 8.0;
+    P.stats.pcg_bytes += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
     P.stats.pcg_launches += 1;
     return it;
 }

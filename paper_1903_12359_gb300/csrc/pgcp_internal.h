@@ -202,29 +202,30 @@ struct SolveResult {
 // Batched PCG on all pieces; x holds fixed values and the initial guess.
 SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, double2* x);
 
-// Double-float PCG (pcg_df.cu): the symmetrically Jacobi-scaled system with
-// fixed rows and columns dropped, its row runs and its work vectors.
+// Run-based PCG (pcg_df.cu): the symmetrically Jacobi-scaled system with
+// fixed rows and columns dropped, its row runs and its work vectors, in
+// double-float (f32 = 0) or FP32 (f32 = 1) arithmetic.
 struct DfRun {
     int32_t seg, lo, hi, frows;
     int32_t fnnz, pad0, pad1, pad2;
 };
 struct DfSystem {
     int64_t n = 0, nnz = 0;
-    int dncp = 0, grid = 0;
+    int dncp = 0, f32 = 0, grid = 0, per_sm = 0, minb = 4;
     int32_t nruns = 0;
     DBuf<int32_t> rp, col;
-    DBuf<float2> val;
-    DBuf<double> sc;      // 1 / sqrt(diag), 0 at fixed rows
-    DBuf<float> dgn;      // diag, 0 at fixed rows
+    DBuf<unsigned char> val;   // nnz scalars (float2 or float)
+    DBuf<double> sc;           // 1 / sqrt(diag), 0 at fixed rows
+    DBuf<float> dgn;           // diag, 0 at fixed rows
     DBuf<DfRun> runs;
     DBuf<int32_t> run_off;
-    DBuf<float4> x, r, p, q;
+    DBuf<unsigned char> x, r, p, q;   // n row pairs (float4 or float2)
     DBuf<double> RR, RD, PQ, THR;
     DBuf<unsigned int> ACT;
     DBuf<int32_t> out_it;
     DBuf<unsigned long long> work;
 };
-void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSystem& D);
+void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D);
 // One inner solve of A d = r64 (thresholds on the unscaled <r, r> per piece
 // and coordinate); adds d to x; returns the iterations run.
 int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x, const std::vector<double>& thr,

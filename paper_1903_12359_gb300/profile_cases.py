@@ -21,6 +21,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--max-iters", type=int, default=300)
     ap.add_argument("--local-precision", type=int, default=2, help="0 FP64 PCG, 2 double-float PCG")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="mixed-precision PCG kernel variant: 3 or 4")
     a = ap.parse_args(argv)
     import torch
     from paper_1903_12359_gb300 import api, build, meshgen
@@ -31,7 +32,8 @@ def main(argv=None):
     L = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
     if a.case == "dncp":
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, max_iters=a.max_iters,
-                          max_refine=1, local_precision=a.local_precision)
+                          max_refine=1, local_precision=a.local_precision,
+                          pcg_blocks_per_sm=a.blocks_per_sm)
         part = ctx.partition(V, F, face_labels=L)
         try:
             part.local_param()
@@ -47,7 +49,7 @@ def main(argv=None):
                           "pcg_launches": st["pcg_launches"]}))
     else:
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10,
-                          local_precision=a.local_precision)
+                          local_precision=a.local_precision, pcg_blocks_per_sm=a.blocks_per_sm)
         part = ctx.partition(V, F, face_labels=L)
         part.local_param()
         part.weld()
