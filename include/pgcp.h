@@ -256,6 +256,21 @@ pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* 
 pgcp_status pgcp_selftest_sort(pgcp_ctx* ctx, uint64_t* keys, int32_t* vals, int64_t n, int32_t bits);
 pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total);
 
+/*
+ * Self-test access to the BF16 tensor-core GEMM of the learned warm start (no
+ * counterpart in the paper).  C[M x N] = epi(A[M x K] . Bt[N x K]^T): A and
+ * Bt bf16, row-major with K contiguous (16-byte aligned), device pointers.
+ *  epilogue 0: C fp32 [M x N];  1: C = relu(. + bias) as bf16;  2: C = . + bias
+ *  (fp32).  Shapes (N, K) in {(16,16), (16,64), (64,16), (64,64), (64,128),
+ *  (128,64)}, else PGCP_E_ARG.  Synchronises the context stream.
+ * pgcp_selftest_umma_desc / _idesc: the shared-memory matrix descriptor and
+ * the instruction descriptor the kernel issues (host computation, no GPU).
+ */
+pgcp_status pgcp_selftest_gemm_bf16(pgcp_ctx* ctx, int32_t epilogue, int32_t N, int32_t K, const void* A,
+                                    const void* Bt, int64_t M, const float* bias, void* C);
+uint64_t pgcp_selftest_umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo);
+uint32_t pgcp_selftest_umma_idesc(int32_t m, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

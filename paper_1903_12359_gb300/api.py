@@ -90,6 +90,9 @@ SIGNATURES = {
                            C.POINTER(Stats)]),
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
     "pgcp_selftest_scan": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
+    "pgcp_selftest_gemm_bf16": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]),
+    "pgcp_selftest_umma_desc": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint32]),
+    "pgcp_selftest_umma_idesc": (C.c_uint32, [C.c_int32, C.c_int32]),
 }
 
 _lib = None
@@ -155,6 +158,16 @@ class Context:
     def check(self, st):
         if st:
             raise PgcpError(st, load().pgcp_last_error(self.h).decode())
+
+    def selftest_gemm_bf16(self, A, Bt, epilogue=0, bias=None):
+        """C = epi(A . Bt^T) on the tensor cores; A [M, K], Bt [N, K] bf16 CUDA tensors."""
+        M, K = A.shape
+        N = Bt.shape[0]
+        dt = torch.bfloat16 if epilogue == 1 else torch.float32
+        C_ = torch.empty((M, N), dtype=dt, device="cuda")
+        self.check(load().pgcp_selftest_gemm_bf16(self.h, epilogue, N, K, _ptr(A.contiguous()), _ptr(Bt.contiguous()),
+                                                  M, _ptr(bias), _ptr(C_)))
+        return C_
 
     def set_options(self, **kw):
         for k, v in kw.items():

@@ -438,4 +438,18 @@ pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, i
     });
 }
 
+pgcp_status pgcp_selftest_gemm_bf16(pgcp_ctx* ctx, int32_t epilogue, int32_t N, int32_t K, const void* A,
+                                    const void* Bt, int64_t M, const float* bias, void* C) {
+    return guard(ctx, [&] {
+        if (!A || !Bt || !C || M < 0) fail(PGCP_E_ARG, "bad GEMM arguments");
+        if (epilogue != 0 && !bias) fail(PGCP_E_ARG, "this epilogue needs a bias");
+        ctx->err.zero();
+        gemm_bf16_tc(ctx->stream, epilogue, N, K, A, K, Bt, M, bias, C, N, nullptr, 0, ctx->err.p);
+        if (read_errors(ctx) & DE_TIMEOUT) fail(PGCP_E_CUDA, "tensor-core GEMM: accumulator wait timed out");
+    });
+}
+
+uint64_t pgcp_selftest_umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) { return umma_desc_host(saddr, lbo, sbo); }
+uint32_t pgcp_selftest_umma_idesc(int32_t m, int32_t n) { return umma_idesc_host(m, n); }
+
 }  // extern "C"

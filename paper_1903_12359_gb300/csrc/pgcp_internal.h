@@ -36,6 +36,7 @@ enum DevErr : uint32_t {
     DE_UNION_LIMIT = 1u << 6,
     DE_WELD_DOMAIN = 1u << 7,
     DE_HASH_FULL = 1u << 8,
+    DE_TIMEOUT = 1u << 9,      // a bounded wait in a kernel gave up
 };
 
 // ------------------------------------------------------------------ device memory
@@ -241,6 +242,14 @@ void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distort
 // Same statistics on a fixed device-side scratch array; no allocation.
 void compute_metrics_noalloc(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
 int64_t metrics_noalloc_max_faces();
+
+// BF16 tensor-core GEMM (gemm_tc.cu): C = epi(A . Bt^T), A [M x K], Bt [N x K],
+// both bf16 with K contiguous.  epi 0: store FP32; 1: + bias, ReLU, store bf16
+// (and the pre-activation to Z if given); 2: + bias, store FP32.
+void gemm_bf16_tc(cudaStream_t s, int epi, int N, int K, const void* A, int64_t lda, const void* Bt, int64_t M,
+                  const float* bias, void* C, int64_t ldc, float* Z, int64_t ldz, uint32_t* err);
+uint64_t umma_desc_host(uint32_t saddr, uint32_t lbo, uint32_t sbo);
+uint32_t umma_idesc_host(int m, int n);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
