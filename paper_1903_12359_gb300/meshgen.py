@@ -494,3 +494,16 @@ def uneven_batch(n_mesh: int = 256, seed: int = 0, nmin: int = 5000, nmax: int =
         ny = int(math.ceil(K / nx))
         out.append(heightfield_disk_mesh(N, seed=seed * 100003 + i, nx=nx, ny=ny, uneven=True))
     return out
+
+
+def he_normal(seed: int, shapes) -> np.ndarray:
+    """Seeded initial parameters: N(0, 2 / fan_in) for matrices (rows = inputs),
+    zeros for vectors, concatenated in order (float64)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shp in shapes:
+        if len(shp) == 2:
+            parts.append(rng.normal(0.0, math.sqrt(2.0 / shp[0]), size=shp).reshape(-1))
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate(parts)
