@@ -89,7 +89,7 @@ typedef struct {
     double  pcg_bytes;         /* algorithmic bytes those launches move: per active free row and
                                   iteration 4 + 25*T, per stored entry of its row 4 + T (T = 4 or 8) */
     int32_t pcg_launches;
-    int32_t pad;
+    int32_t learned_pieces;    /* pieces whose final solve started from the learned prediction */
 } pgcp_stats;
 
 /* Angle-distortion statistics of a result (Section 5 definition, degrees). */
@@ -103,6 +103,7 @@ typedef struct {
 
 typedef struct pgcp_ctx pgcp_ctx;    /* opaque; one per CUDA stream */
 typedef struct pgcp_part pgcp_part;  /* opaque; partition + all per-piece device state */
+typedef struct pgcp_gnn pgcp_gnn;    /* opaque; learned warm-start network (parameters, optimiser state) */
 
 /* Default options: DISK, FP32_REFINED, tol 1e-10, 200000 iterations, 8 refinement
  * steps, inner_tol 1e-4, weld-map warm start, FP32 interior map. */
@@ -243,6 +244,47 @@ pgcp_status pgcp_metrics_noalloc(pgcp_ctx* ctx, const pgcp_part* part, const dou
 pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
                      const int32_t* cut_edges, int64_t n_cut, const int32_t* face_labels,
                      int32_t host_ptrs, double* out, pgcp_stats* st);
+
+/*
+ * Learned warm start (no counterpart in the paper).  A message-passing network
+ * over each piece's mesh graph predicts the correction from the weld-map
+ * start u_w to the final map; the final solve (Section 4.5) starts from
+ * u_w + sigma * prediction on the pieces where that start has the smaller
+ * FP64 residual, and from u_w elsewhere, so the result does not depend on the
+ * network.  Architecture, features and parameter layout:
+ *   F_i = [z_i / sigma, boundary flag, 1, 0 x 12] (16 wide), z_i = -(L u_w)_i / d_i
+ *         on interior rows, sigma = RMS of |z| over the piece's interior rows;
+ *   X_0 = relu(F W_in + b_in);  X_{l+1} = relu([X_l | P X_l] W_l + b_l), l = 0..3,
+ *         P = D^-1 W the random walk of the cotan weights;  out = X_4 W_out + b_out.
+ *   Parameters, one float32 vector of pgcp_gnn_num_params() = 35152 values:
+ *   W_in (16 x 64), b_in (64), 4 x [W_l (128 x 64), b_l (64)], W_out (64 x 16),
+ *   b_out (16); matrices row-major with rows = inputs.  Dense layers run in
+ *   BF16 on the tensor cores with FP32 accumulation.
+ * A part is usable for prediction after pgcp_weld, for training after
+ * pgcp_global_solve (the target is its final map).
+ *  pgcp_gnn_create: params = host float32 [num_params] (initial values).
+ *  pgcp_gnn_load: the same from a raw little-endian float32 file.
+ *  pgcp_set_gnn: network used by warm_start = PGCP_WARM_LEARNED (not owned;
+ *    NULL detaches).
+ *  pgcp_gnn_inputs: features feat [rows x 16] (float32, the bf16 values the
+ *    network sees), targets [rows x 2] (may be NULL; needs the final map) and
+ *    sigma [K], all device pointers, rows = vertex copies (pgcp_part_info).
+ *  pgcp_gnn_grad: loss (mean over interior rows of |out - target|^2) and its
+ *    gradient (host float32 [num_params]) at the current parameters.
+ *  pgcp_gnn_train_step: one Adam step (lr) on that loss; *loss before the step.
+ *  pgcp_gnn_predict: x0 [rows x 2] (device, FP64) = u_w + sigma * out.
+ */
+int64_t pgcp_gnn_num_params(void);
+pgcp_status pgcp_gnn_create(pgcp_ctx* ctx, const float* params, pgcp_gnn** out);
+pgcp_status pgcp_gnn_load(pgcp_ctx* ctx, const char* path, pgcp_gnn** out);
+pgcp_status pgcp_gnn_free(pgcp_gnn* gnn);
+pgcp_status pgcp_gnn_get_params(pgcp_ctx* ctx, const pgcp_gnn* gnn, float* params);
+pgcp_status pgcp_gnn_set_params(pgcp_ctx* ctx, pgcp_gnn* gnn, const float* params);
+pgcp_status pgcp_set_gnn(pgcp_ctx* ctx, pgcp_gnn* gnn);
+pgcp_status pgcp_gnn_inputs(pgcp_ctx* ctx, const pgcp_part* part, float* feat, float* target, float* sigma);
+pgcp_status pgcp_gnn_grad(pgcp_ctx* ctx, pgcp_gnn* gnn, const pgcp_part* part, float* grad, double* loss);
+pgcp_status pgcp_gnn_train_step(pgcp_ctx* ctx, pgcp_gnn* gnn, const pgcp_part* part, float lr, double* loss);
+pgcp_status pgcp_gnn_predict(pgcp_ctx* ctx, const pgcp_gnn* gnn, const pgcp_part* part, double* x0);
 
 /*
  * Self-test access to the device primitives the partition and the metrics

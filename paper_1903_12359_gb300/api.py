@@ -21,6 +21,8 @@ METRICS_NOALLOC_MAX_FACES = 262144   # PGCP_METRICS_NOALLOC_MAX_FACES
 FREE, DISK, SPHERE = 0, 1, 2
 FP64, FP32_REFINED, DF64_REFINED = 0, 1, 2
 WARM_COLD, WARM_WELDMAP, WARM_LEARNED = 0, 1, 2
+# parameter layout of the learned warm-start network (pgcp.h): matrices rows = inputs
+GNN_PARAM_SHAPES = [(16, 64), (64,)] + [(128, 64), (64,)] * 4 + [(64, 16), (16,)]
 
 STATUS = {0: "OK", 1: "ARG", 2: "CUDA", 3: "OOM", 4: "NONMANIFOLD", 5: "TOPOLOGY", 6: "SCHEDULE",
           7: "DEGENERATE", 8: "NO_CONVERGENCE", 9: "NUMERIC"}
@@ -46,7 +48,7 @@ class Stats(C.Structure):
                 ("final_relres", C.c_double), ("seam_mismatch", C.c_double), ("ms_partition", C.c_double),
                 ("ms_assembly", C.c_double), ("ms_local", C.c_double), ("ms_weld", C.c_double),
                 ("ms_final", C.c_double), ("nnz", C.c_int64), ("n_copies", C.c_int64), ("pcg_ms", C.c_double),
-                ("pcg_bytes", C.c_double), ("pcg_launches", C.c_int32), ("pad", C.c_int32)]
+                ("pcg_bytes", C.c_double), ("pcg_launches", C.c_int32), ("learned_pieces", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +93,17 @@ SIGNATURES = {
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
     "pgcp_selftest_scan": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgcp_selftest_gemm_bf16": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]),
+    "pgcp_gnn_num_params": (C.c_int64, []),
+    "pgcp_gnn_create": (C.c_int, [_P, _P, C.POINTER(C.c_void_p)]),
+    "pgcp_gnn_load": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "pgcp_gnn_free": (C.c_int, [_P]),
+    "pgcp_gnn_get_params": (C.c_int, [_P, _P, _P]),
+    "pgcp_gnn_set_params": (C.c_int, [_P, _P, _P]),
+    "pgcp_set_gnn": (C.c_int, [_P, _P]),
+    "pgcp_gnn_inputs": (C.c_int, [_P, _P, _P, _P, _P]),
+    "pgcp_gnn_grad": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double)]),
+    "pgcp_gnn_train_step": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_double)]),
+    "pgcp_gnn_predict": (C.c_int, [_P, _P, _P, _P]),
     "pgcp_selftest_umma_desc": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint32]),
     "pgcp_selftest_umma_idesc": (C.c_uint32, [C.c_int32, C.c_int32]),
 }
@@ -168,6 +181,11 @@ class Context:
         self.check(load().pgcp_selftest_gemm_bf16(self.h, epilogue, N, K, _ptr(A.contiguous()), _ptr(Bt.contiguous()),
                                                   M, _ptr(bias), _ptr(C_)))
         return C_
+
+    def set_gnn(self, gnn):
+        """Network for warm_start = WARM_LEARNED (None detaches)."""
+        self._gnn = gnn
+        self.check(load().pgcp_set_gnn(self.h, None if gnn is None else gnn.h))
 
     def set_options(self, **kw):
         for k, v in kw.items():
@@ -327,3 +345,70 @@ class Part:
             self.free()
         except Exception:
             pass
+
+
+class Gnn:
+    """The learned warm-start network (parameters live on the device)."""
+
+    def __init__(self, ctx: Context, params=None, path: str | None = None):
+        self.ctx = ctx
+        h = C.c_void_p()
+        if path is not None:
+            ctx.check(load().pgcp_gnn_load(ctx.h, path.encode(), C.byref(h)))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            if p.size != num_gnn_params():
+                raise ValueError(f"expected {num_gnn_params()} parameters, got {p.size}")
+            ctx.check(load().pgcp_gnn_create(ctx.h, p.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.h = h
+
+    def params(self) -> np.ndarray:
+        p = np.empty(num_gnn_params(), dtype=np.float32)
+        self.ctx.check(load().pgcp_gnn_get_params(self.ctx.h, self.h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self.ctx.check(load().pgcp_gnn_set_params(self.ctx.h, self.h, p.ctypes.data_as(C.c_void_p)))
+
+    def grad(self, part):
+        g = np.empty(num_gnn_params(), dtype=np.float32)
+        l = C.c_double()
+        self.ctx.check(load().pgcp_gnn_grad(self.ctx.h, self.h, part.h, g.ctypes.data_as(C.c_void_p), C.byref(l)))
+        return g, l.value
+
+    def train_step(self, part, lr: float) -> float:
+        l = C.c_double()
+        self.ctx.check(load().pgcp_gnn_train_step(self.ctx.h, self.h, part.h, C.c_float(lr), C.byref(l)))
+        return l.value
+
+    def predict(self, part):
+        rows = part.info()["n_copies"]
+        x = torch.empty((rows, 2), dtype=torch.float64, device="cuda")
+        self.ctx.check(load().pgcp_gnn_predict(self.ctx.h, self.h, part.h, _ptr(x)))
+        return x
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().pgcp_gnn_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def num_gnn_params() -> int:
+    return int(load().pgcp_gnn_num_params())
+
+
+def gnn_inputs(part, targets: bool = True):
+    """(features [rows, 16], targets [rows, 2] or None, sigma [K]) as CUDA tensors."""
+    i = part.info()
+    feat = torch.empty((i["n_copies"], 16), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((i["n_copies"], 2), dtype=torch.float32, device="cuda") if targets else None
+    sig = torch.empty(i["K"], dtype=torch.float32, device="cuda")
+    part.ctx.check(load().pgcp_gnn_inputs(part.ctx.h, part.h, _ptr(feat), _ptr(tgt), _ptr(sig)))
+    return feat, tgt, sig

@@ -438,6 +438,106 @@ pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, i
     });
 }
 
+int64_t pgcp_gnn_num_params(void) { return gnn_num_params(); }
+
+pgcp_status pgcp_gnn_create(pgcp_ctx* ctx, const float* params, pgcp_gnn** out) {
+    return guard(ctx, [&] {
+        if (!ctx || !params || !out) fail(PGCP_E_ARG, "null argument");
+        *out = nullptr;
+        auto* g = new pgcp_gnn();
+        try {
+            gnn_init(ctx, g, params);
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+    });
+}
+
+pgcp_status pgcp_gnn_load(pgcp_ctx* ctx, const char* path, pgcp_gnn** out) {
+    return guard(ctx, [&] {
+        if (!ctx || !path || !out) fail(PGCP_E_ARG, "null argument");
+        FILE* f = std::fopen(path, "rb");
+        if (!f) fail(PGCP_E_ARG, std::string("cannot open ") + path);
+        std::vector<float> v((size_t)gnn_num_params());
+        const size_t got = std::fread(v.data(), sizeof(float), v.size(), f);
+        const bool extra = std::fgetc(f) != EOF;
+        std::fclose(f);
+        if (got != v.size() || extra) fail(PGCP_E_ARG, std::string("wrong parameter count in ") + path);
+        *out = nullptr;
+        auto* g = new pgcp_gnn();
+        try {
+            gnn_init(ctx, g, v.data());
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+    });
+}
+
+pgcp_status pgcp_gnn_free(pgcp_gnn* gnn) {
+    delete gnn;
+    return PGCP_OK;
+}
+
+pgcp_status pgcp_gnn_get_params(pgcp_ctx* ctx, const pgcp_gnn* gnn, float* params) {
+    return guard(ctx, [&] {
+        if (!ctx || !gnn || !params) fail(PGCP_E_ARG, "null argument");
+        gnn_get(ctx, gnn, params);
+    });
+}
+
+pgcp_status pgcp_gnn_set_params(pgcp_ctx* ctx, pgcp_gnn* gnn, const float* params) {
+    return guard(ctx, [&] {
+        if (!ctx || !gnn || !params) fail(PGCP_E_ARG, "null argument");
+        gnn_set(ctx, gnn, params);
+    });
+}
+
+pgcp_status pgcp_set_gnn(pgcp_ctx* ctx, pgcp_gnn* gnn) {
+    return guard(ctx, [&] {
+        if (!ctx) fail(PGCP_E_ARG, "null context");
+        if (gnn && gnn->device != ctx->device) fail(PGCP_E_ARG, "network and context are on different devices");
+        ctx->gnn = gnn;
+    });
+}
+
+pgcp_status pgcp_gnn_inputs(pgcp_ctx* ctx, const pgcp_part* part, float* feat, float* target, float* sigma) {
+    return guard(ctx, [&] {
+        if (!ctx || !part || !feat || !sigma) fail(PGCP_E_ARG, "null argument");
+        gnn_inputs(ctx, const_cast<Part&>(part->p), feat, target, sigma);
+    });
+}
+
+pgcp_status pgcp_gnn_grad(pgcp_ctx* ctx, pgcp_gnn* gnn, const pgcp_part* part, float* grad, double* loss) {
+    return guard(ctx, [&] {
+        if (!ctx || !gnn || !part || !grad) fail(PGCP_E_ARG, "null argument");
+        const double l = gnn_grad(ctx, gnn, const_cast<Part&>(part->p), 0, 0.f);
+        PGCP_CUDA(cudaMemcpyAsync(grad, gnn->grad.p, gnn_num_params() * sizeof(float), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+        PGCP_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (loss) *loss = l;
+    });
+}
+
+pgcp_status pgcp_gnn_train_step(pgcp_ctx* ctx, pgcp_gnn* gnn, const pgcp_part* part, float lr, double* loss) {
+    return guard(ctx, [&] {
+        if (!ctx || !gnn || !part) fail(PGCP_E_ARG, "null argument");
+        if (!(lr > 0.f)) fail(PGCP_E_ARG, "learning rate must be positive");
+        const double l = gnn_grad(ctx, gnn, const_cast<Part&>(part->p), 1, lr);
+        if (loss) *loss = l;
+    });
+}
+
+pgcp_status pgcp_gnn_predict(pgcp_ctx* ctx, const pgcp_gnn* gnn, const pgcp_part* part, double* x0) {
+    return guard(ctx, [&] {
+        if (!ctx || !gnn || !part || !x0) fail(PGCP_E_ARG, "null argument");
+        gnn_predict(ctx, gnn, const_cast<Part&>(part->p), reinterpret_cast<double2*>(x0));
+    });
+}
+
 pgcp_status pgcp_selftest_gemm_bf16(pgcp_ctx* ctx, int32_t epilogue, int32_t N, int32_t K, const void* A,
                                     const void* Bt, int64_t M, const float* bias, void* C) {
     return guard(ctx, [&] {

@@ -165,6 +165,13 @@ struct Part {
 
 // ------------------------------------------------------------------ context
 
+struct pgcp_gnn {
+    int device = 0;
+    pgcp::DBuf<float> theta, grad, m, v;   // FP32 parameters, gradient, Adam moments
+    pgcp::DBuf<uint16_t> bf;               // bf16 weight copies laid out for the GEMMs
+    int64_t step = 0;
+};
+
 struct pgcp_ctx {
     pgcp_options opt;
     cudaStream_t stream = nullptr;
@@ -172,6 +179,7 @@ struct pgcp_ctx {
     int num_sms = 0;
     std::string last_error;
     pgcp::DBuf<uint32_t> err;        // device error flags
+    pgcp_gnn* gnn = nullptr;         // network for warm_start = PGCP_WARM_LEARNED (not owned)
 };
 
 struct pgcp_part {
@@ -249,6 +257,16 @@ int64_t metrics_noalloc_max_faces();
 void gemm_bf16_tc(cudaStream_t s, int epi, int N, int K, const void* A, int64_t lda, const void* Bt, int64_t M,
                   const float* bias, void* C, int64_t ldc, float* Z, int64_t ldz, uint32_t* err);
 uint64_t umma_desc_host(uint32_t saddr, uint32_t lbo, uint32_t sbo);
+
+// Learned warm start (mpnn.cu)
+int64_t gnn_num_params();
+void gnn_init(pgcp_ctx* ctx, pgcp_gnn* G, const float* host_params);
+void gnn_set(pgcp_ctx* ctx, pgcp_gnn* G, const float* host_params);
+void gnn_get(pgcp_ctx* ctx, const pgcp_gnn* G, float* host_params);
+void gnn_inputs(pgcp_ctx* ctx, Part& P, float* feat, float* target, float* sigma);
+double gnn_grad(pgcp_ctx* ctx, pgcp_gnn* G, Part& P, int update, float lr);
+void gnn_predict(pgcp_ctx* ctx, const pgcp_gnn* G, Part& P, double2* x);
+int learned_start(pgcp_ctx* ctx, Part& P, double2* x);
 uint32_t umma_idesc_host(int m, int n);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

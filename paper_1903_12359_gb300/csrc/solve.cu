@@ -140,6 +140,8 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     { k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.welded.p, ctx->opt.warm_start == PGCP_WARM_COLD,
                                          P.final.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
+    P.stats.learned_pieces = 0;
+    if (ctx->opt.warm_start == PGCP_WARM_LEARNED) P.stats.learned_pieces = learned_start(ctx, P, P.final.p);
     SolveResult r = pcg_solve(ctx, P, 0, P.is_bnd.p, P.final.p);
     P.stats.final_iters = r.iters;
     P.stats.final_refine = r.refine;
