@@ -157,13 +157,24 @@ def _piece_loop(Fi: np.ndarray, vi: np.ndarray, piece: int) -> np.ndarray:
 
 @dataclass
 class Weld:
-    piece: int              # S, the piece joined to the component C
-    a: np.ndarray           # C's loop rotated so a[0..k] is the shared arc (global ids)
-    b: np.ndarray           # S's loop reversed, rotated so b[j] == a[j] for j <= k
+    piece: int              # lowest label of B, the component joined to A
+    a: np.ndarray           # A's loop rotated so a[0..k] is the shared arc (global ids)
+    b: np.ndarray           # B's loop reversed, rotated so b[j] == a[j] for j <= k
     k: int                  # number of shared edges
     closed: bool            # the whole loop is shared (closed welding, Section 4.4.2)
-    members: list           # pieces of C before this weld (ascending)
-    new_loop: np.ndarray    # C's loop after this weld (ccw, canonical start)
+    members: list           # pieces of A (ascending)
+    new_loop: np.ndarray    # loop of A u B after this weld (ccw, canonical start)
+    b_members: list = field(default_factory=list)   # pieces of B (ascending)
+    a_single: bool = True   # A is one unwelded piece (its reference point is 0, else -1)
+    b_single: bool = True
+    level: int = 0          # welds of one level join disjoint components
+
+
+@dataclass
+class _Comp:
+    members: list
+    loop: np.ndarray
+    single: bool
 
 
 def _rotate_canonical(loop: np.ndarray) -> np.ndarray:
@@ -171,71 +182,97 @@ def _rotate_canonical(loop: np.ndarray) -> np.ndarray:
     return np.concatenate([loop[i:], loop[:i]])
 
 
-def weld_schedule(P: Partition, closed_surface: bool) -> list:
-    """Order of the partial welds.
+def _pair_weld(A: _Comp, B: _Comp, closed_final: bool):
+    """The weld of B onto A, or None unless their loops share exactly one
+    contiguous arc of >= 2 edges and touch nowhere else (A u B is then a
+    disk); on a closed surface the final two components share the whole loop."""
+    A_loop, B_loop = A.loop, B.loop
+    b_edges = set(zip(B_loop.tolist(), np.roll(B_loop, -1).tolist()))
+    m1 = A_loop.size
+    nxt = np.roll(A_loop, -1)
+    shared = np.array([(int(v), int(u)) in b_edges for u, v in zip(A_loop, nxt)])
+    if not shared.any():
+        return None
+    rb = B_loop[::-1]
 
-    Reading (the paper only shows sequential welding): the component C starts
-    as piece 0; each step joins the lowest-label piece S whose shared boundary
-    with C is ONE contiguous arc of >= 2 edges and touches C nowhere else (so
-    C u S stays a disk).  On a closed surface the last piece shares its whole
-    loop and is joined by a closed weld.
+    def plan(a, b, k, closed, new_loop):
+        return Weld(piece=B.members[0], a=a, b=b, k=k, closed=closed, members=list(A.members), new_loop=new_loop,
+                    b_members=list(B.members), a_single=A.single, b_single=B.single)
+
+    if shared.all():
+        if not (closed_final and B_loop.size == m1):
+            return None
+        a = A_loop.copy()
+        j = int(np.nonzero(rb == a[0])[0][0])
+        b = np.concatenate([rb[j:], rb[:j]])
+        if not np.array_equal(a, b):
+            return None
+        return plan(a, b, m1 - 1, True, np.zeros(0, dtype=np.int64))
+    starts = np.nonzero(shared & ~np.roll(shared, 1))[0]
+    if starts.size != 1:
+        return None
+    i0 = int(starts[0])
+    rs = np.roll(shared, -i0)
+    k = int(np.argmin(rs))
+    if k < 2:
+        return None
+    a = np.concatenate([A_loop[i0:], A_loop[:i0]])
+    if set(A_loop.tolist()) & set(B_loop.tolist()) != set(a[:k + 1].tolist()):
+        return None
+    j = int(np.nonzero(rb == a[0])[0][0])
+    b = np.concatenate([rb[j:], rb[:j]])
+    if not np.array_equal(a[:k + 1], b[:k + 1]):
+        return None
+    new_loop = _rotate_canonical(np.concatenate([a[k:], a[:1], b[k + 1:][::-1]]))
+    return plan(a, b, k, False, new_loop)
+
+
+def weld_schedule(P: Partition, closed_surface: bool) -> list:
+    """Order of the partial welds, by levels.
+
+    Reading: the paper welds one piece at a time onto a growing component
+    (Fig. 7), but Algorithm 2 joins any two disks that share one boundary arc.
+    Sequential welding composes K elementary chains on the first piece's
+    boundary, and with 16-36 pieces the crowding of that boundary makes the
+    FP64 zipper lose the order of the arc.  Here components are instead paired
+    level by level, so a piece's boundary passes through about log2 K welds:
+    * the components start as the pieces, ordered by lowest label;
+    * in each level, every unpaired component, in that order, is paired with
+      the first later unpaired component that shares ONE contiguous arc of >= 2
+      edges of its loop and touches it nowhere else, so the union stays a disk;
+      the earlier component is A, the later one B;
+    * the welds of a level join disjoint components;
+    * on a closed surface the last two components share their whole loops and
+      are joined by a closed weld.
     """
     K = P.K
     if K == 1:
         return []
-    C_loop = P.loops[0].copy()
-    members = [0]
-    remaining = list(range(1, K))
+    comps = [_Comp([i], P.loops[i].copy(), True) for i in range(K)]
     welds = []
-    while remaining:
-        chosen = None
-        for s in remaining:
-            S_loop = P.loops[s]
-            s_edges = set(zip(S_loop.tolist(), np.roll(S_loop, -1).tolist()))
-            m1 = C_loop.size
-            nxt = np.roll(C_loop, -1)
-            shared = np.array([(int(v), int(u)) in s_edges for u, v in zip(C_loop, nxt)])
-            if not shared.any():
+    level = 0
+    while len(comps) > 1:
+        final2 = closed_surface and len(comps) == 2
+        used = [False] * len(comps)
+        merged = []
+        for i in range(len(comps)):
+            if used[i]:
                 continue
-            if shared.all():
-                if not (closed_surface and len(remaining) == 1 and S_loop.size == m1):
+            for j in range(i + 1, len(comps)):
+                if used[j]:
                     continue
-                a = C_loop.copy()
-                rb = S_loop[::-1]
-                j = int(np.nonzero(rb == a[0])[0][0])
-                b = np.concatenate([rb[j:], rb[:j]])
-                if not np.array_equal(a, b):
+                w = _pair_weld(comps[i], comps[j], final2)
+                if w is None:
                     continue
-                chosen = Weld(piece=s, a=a, b=b, k=m1 - 1, closed=True,
-                              members=sorted(members), new_loop=np.zeros(0, dtype=np.int64))
+                w.level = level
+                welds.append(w)
+                used[i] = used[j] = True
+                merged.append(_Comp(sorted(comps[i].members + comps[j].members), w.new_loop, False))
                 break
-            starts = np.nonzero(shared & ~np.roll(shared, 1))[0]
-            if starts.size != 1:
-                continue
-            i0 = int(starts[0])
-            rs = np.roll(shared, -i0)
-            k = int(np.argmin(rs)) if not rs.all() else m1
-            if k < 2:
-                continue
-            a = np.concatenate([C_loop[i0:], C_loop[:i0]])
-            common = set(C_loop.tolist()) & set(S_loop.tolist())
-            if common != set(a[:k + 1].tolist()):
-                continue
-            rb = S_loop[::-1]
-            j = int(np.nonzero(rb == a[0])[0][0])
-            b = np.concatenate([rb[j:], rb[:j]])
-            if not np.array_equal(a[:k + 1], b[:k + 1]):
-                continue
-            new_loop = np.concatenate([a[k:], a[:1], b[k + 1:][::-1]])
-            chosen = Weld(piece=s, a=a, b=b, k=k, closed=False, members=sorted(members),
-                          new_loop=_rotate_canonical(new_loop))
-            break
-        if chosen is None:
-            raise OracleError("SCHEDULE", "no piece shares one contiguous arc with the welded component")
-        welds.append(chosen)
-        members.append(chosen.piece)
-        remaining.remove(chosen.piece)
-        C_loop = chosen.new_loop
+        if not merged:
+            raise OracleError("SCHEDULE", "no two components share one contiguous arc")
+        comps = sorted(merged + [c for c, u in zip(comps, used) if not u], key=lambda c: c.members[0])
+        level += 1
     if closed_surface and not welds[-1].closed:
         raise OracleError("SCHEDULE", "closed surface did not end with a closed weld")
     return welds

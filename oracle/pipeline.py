@@ -8,14 +8,16 @@ boundary (Sec. 4.5) -> gather (lowest label wins) -> stereographic projection
 for the sphere.
 
 Readings (listed in full in the design notes; the CUDA library follows them):
-* auxiliary points of a weld: a_{m+1} is C's reference point (0 for a single
-  DNCP piece, -1 -- the value the normalisation gives it -- for a welded
-  component), b_{n+1} = 0 (S's reference), a_{m+2} = b_{n+2} = inf;
+* auxiliary points of a weld of B onto A: a_{m+1} and b_{n+1} are the
+  components' reference points (0 for a single DNCP piece, -1 -- the value
+  the normalisation gives A's reference -- for a welded component),
+  a_{m+2} = b_{n+2} = inf;
+* welds run by levels of disjoint pairs (see mesh.weld_schedule);
 * the final normalisation takes the midpoint of a~_{m+2} and b~_{n+2}
   (the paper's "a~_{n+2}" is read as b~_{n+2});
 * the closed weld of a sphere normalises with p1 = a~_{m+1} -> 0,
-  p2 = b~_{n+1} -> inf, a~_{floor(k/2)} -> 1; the last piece is then held in
-  the chart w = 1/z; the projection (2x, -2y, |z|^2 - 1)/(1 + |z|^2), i.e.
+  p2 = b~_{n+1} -> inf, a~_{floor(k/2)} -> 1; the pieces of its B component
+  are then held in the chart w = 1/z; the projection (2x, -2y, |z|^2 - 1)/(1 + |z|^2), i.e.
   (2 Re w, 2 Im w, 1 - |w|^2)/(1 + |w|^2) in that chart, keeps orientation.
 """
 from __future__ import annotations
@@ -45,40 +47,44 @@ class Result:
     disk_chain: list = None
     final: list = field(default_factory=list)     # per piece coords after the Laplace solve
     out: np.ndarray = None                        # gathered [nv, 2] or [nv, 3]
-    sphere_w_piece: int = -1                      # piece held in the w = 1/z chart
+    sphere_w_pieces: list = field(default_factory=list)   # pieces held in the w = 1/z chart
     seam_mismatch: float = 0.0
 
 
-def _weld_once(res: Result, wd, ref_C: float, map_interior: bool, sphere_close: bool):
+def _weld_once(res: Result, wd, map_interior: bool, sphere_close: bool):
     P = res.part
     k = wd.k
-    m = wd.a.size - 1
-    n = wd.b.size - 1
     members = wd.members
-    # coordinates of C's loop points: the copy in the lowest-label member holding it
-    pos = {}
-    for pc in members:
-        for li, g in enumerate(P.verts[pc].tolist()):
-            pos.setdefault(g, (pc, li))
-    a_re = np.empty(m + 1)
-    a_im = np.empty(m + 1)
-    for j, g in enumerate(wd.a.tolist()):
-        pc, li = pos[g]
-        a_re[j] = res.welded[pc].real[li]
-        a_im[j] = res.welded[pc].imag[li]
-    s = wd.piece
-    sl = {g: li for li, g in enumerate(P.verts[s].tolist())}
-    b_loc = np.array([sl[g] for g in wd.b.tolist()])
-    b_re = res.welded[s].real[b_loc]
-    b_im = res.welded[s].imag[b_loc]
+    b_members = wd.b_members
+
+    def loop_coords(pieces, ids):
+        # each loop point from the copy in the lowest-label piece of the side holding it
+        pos = {}
+        for pc in pieces:
+            for li, g in enumerate(P.verts[pc].tolist()):
+                pos.setdefault(g, (pc, li))
+        re_ = np.empty(ids.size)
+        im_ = np.empty(ids.size)
+        for j, g in enumerate(ids.tolist()):
+            pc, li = pos[g]
+            re_[j] = res.welded[pc].real[li]
+            im_[j] = res.welded[pc].imag[li]
+        return re_, im_
+
+    a_re, a_im = loop_coords(members, wd.a)
+    b_re, b_im = loop_coords(b_members, wd.b)
+    # reference points: 0 in a single piece's DNCP frame, -1 (where the
+    # normalisation sends A's reference) for a welded component
+    ref_A = 0.0 if wd.a_single else -1.0
+    ref_B = 0.0 if wd.b_single else -1.0
     Aarc = W.Pts(a_re[:k + 1], a_im[:k + 1])
     Barc = W.Pts(b_re[:k + 1], b_im[:k + 1])
     gA, Aimg = W.intermediate_form(Aarc, k, +1.0)
     gB, Bimg = W.intermediate_form(Barc, k, -1.0)
     hs, X, Y = W.weld_maps(Aimg, Bimg, k)
     # auxiliary points through each side's chain
-    auxA = W.apply_chain(gA + hs, W.Pts([ref_C, 0.0], [0.0, 0.0], [False, True]))
-    auxB = W.apply_chain(gB + hs, W.Pts([0.0, 0.0], [0.0, 0.0], [False, True]))
+    auxA = W.apply_chain(gA + hs, W.Pts([ref_A, 0.0], [0.0, 0.0], [False, True]))
+    auxB = W.apply_chain(gB + hs, W.Pts([ref_B, 0.0], [0.0, 0.0], [False, True]))
     if auxA.inf.any() or auxB.inf.any():
         raise OracleError("NUMERIC", "auxiliary point mapped to infinity")
     p1 = complex(auxA.re[0], auxA.im[0])
@@ -91,13 +97,13 @@ def _weld_once(res: Result, wd, ref_C: float, map_interior: bool, sphere_close: 
         p3 = complex((auxA.re[1] + auxB.re[1]) * 0.5, (auxA.im[1] + auxB.im[1]) * 0.5)
         TA = TB = W.rec_normalize(p1, p2, p3)
     arc_A = W.apply_rec(TA, X)      # final images of the arc points (C side)
-    arc_B = W.apply_rec(TB, Y)      # same points in S's chart (sphere) / same values
+    arc_B = W.apply_rec(TB, Y)      # same points in B's chart (sphere) / same values
     chainA = gA + hs + [TA]
     chainB = gB + hs + [TB]
     res.weld_chains.append((chainA, chainB))
     arc_pos = {g: j for j, g in enumerate(wd.a[:k + 1].tolist())}
     # apply to every point of every involved piece
-    for pc, chain, arc in [(pc, chainA, arc_A) for pc in members] + [(s, chainB, arc_B)]:
+    for pc, chain, arc in [(pc, chainA, arc_A) for pc in members] + [(pc, chainB, arc_B) for pc in b_members]:
         g_ids = P.verts[pc]
         on_loop = np.zeros(g_ids.size, dtype=bool)
         gl = {g: li for li, g in enumerate(g_ids.tolist())}
@@ -221,10 +227,10 @@ def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
         res.welded.append(u.copy())
         res.welded_inf.append(np.zeros(u.size, dtype=bool))
         loop_local.append(ll)
-    for wi, wd in enumerate(welds):
-        _weld_once(res, wd, 0.0 if wi == 0 else -1.0, map_interior, sphere_close=wd.closed)
+    for wd in welds:
+        _weld_once(res, wd, map_interior, sphere_close=wd.closed)
     if variant == "sphere":
-        res.sphere_w_piece = welds[-1].piece
+        res.sphere_w_pieces = list(welds[-1].b_members)
     if variant == "disk":
         _disk_step(res, map_interior)
     # final Laplace solves with the welded boundary
@@ -243,7 +249,7 @@ def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
     for i in range(P.K):
         g = P.verts[i]
         if variant == "sphere":
-            xyz = stereo_from_inverted(res.final[i]) if i == res.sphere_w_piece else stereo_from_plane(res.final[i])
+            xyz = stereo_from_inverted(res.final[i]) if i in res.sphere_w_pieces else stereo_from_plane(res.final[i])
             have = ~np.isnan(out[g, 0])
             if have.any():
                 mism = max(mism, float(np.abs(out[g[have]] - xyz[have]).max()))

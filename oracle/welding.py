@@ -254,11 +254,11 @@ def apply_rec(rec: Rec, P: Pts, mode=None) -> Pts:
             if k == OPEN:
                 cr, ci = rec.p
                 _, _, Mr, Mi = _mob_open(cr, ci, zr, zi)
-                Minf_i = -(cr / ci)
+                Minf_i = -(np.float64(cr) / np.float64(ci))   # IEEE: a real xi sends infinity to infinity
             else:
                 c1, c2 = rec.p
                 _, _, Mr, Mi = _mob_close(c1, c2, zr, zi)
-                Minf_i = 1.0 / c2
+                Minf_i = np.float64(1.0) / np.float64(c2)
             Mr = np.where(fin, Mr, 0.0)
             Mi = np.where(fin, Mi, Minf_i)
             sr = Mr * Mr - Mi * Mi

@@ -47,7 +47,7 @@ def _sphere_to_plane(p):
 @pytest.mark.slow
 def test_round_sphere_is_a_mobius_image():
     res = []
-    for sd in (3, 4, 5):
+    for sd in (4, 5, 6):     # subdivision 3 (642 vertices) is still pre-asymptotic
         m = meshgen.icosphere_sh_mesh(subdiv=sd, seed=0, amp=0.0)
         r = pgcp(m.V, m.F, face_labels=m.face_labels, variant="sphere")
         assert np.abs(np.linalg.norm(r.out, axis=1) - 1).max() < 1e-14
@@ -56,7 +56,7 @@ def test_round_sphere_is_a_mobius_image():
             z, w = _sphere_to_plane(P), _sphere_to_plane(r.out)
         ok = (np.abs(z) < 5) & (np.abs(w) < 5)
         res.append(_mobius_fit_residual(z[ok], w[ok]))
-    assert res[-1] < 5e-3
+    assert res[-1] < 1e-3
     assert res[0] / res[1] > 2.5 and res[1] / res[2] > 2.5
 
 
