@@ -274,10 +274,17 @@ def main():
     value = ws * m.nv * args.steps / (ms / 1000.0)
     # plain form: cold start of the final solve (same pipeline otherwise)
     value_cold, stats_cold = None, [{"final_iters": None}]
+    value_learned, stats_learned = None, [{"final_iters": None, "learned_pieces": None}]
     if not args.no_cold:
         ctx_cold = make_ctx(api.WARM_COLD)
         ms_cold, stats_cold, _, _ = timed(ctx_cold, 2, 1)
         value_cold = ws * m.nv * 2 / (ms_cold / 1000.0)
+        # learned form: the trained network's prediction, verified per piece
+        ctx_l = make_ctx(api.WARM_LEARNED)
+        gnn = api.Gnn(ctx_l, path=os.path.join(ROOT, "paper_1903_12359_gb300", "weights", "mpnn_disk.bin"))
+        ctx_l.set_gnn(gnn)
+        ms_l, stats_learned, _, _ = timed(ctx_l, 2, 1)
+        value_learned = ws * m.nv * 2 / (ms_l / 1000.0)
     # end to end through the one-shot C call with host buffers
     e2e = None
     if not args.no_e2e:
@@ -336,10 +343,12 @@ def main():
                        ("double-float PCG in FP64 refinement" if df else "FP64 PCG"), "warm_start": "weld map",
                        "l2": "flushed before every step (256 MB write)",
                        "plain_cold_start_value": value_cold,
-                       "learned_warm_start": "not built yet"},
+                       "learned_warm_start_value": value_learned,
+                       "learned_pieces": stats_learned[-1]["learned_pieces"]},
             "stages_ms": {k: s0[k] for k in ("ms_partition", "ms_assembly", "ms_local", "ms_weld", "ms_final")},
             "iterations": {"dncp": s0["dncp_iters"], "final": s0["final_iters"],
-                           "final_cold": stats_cold[-1]["final_iters"]},
+                           "final_cold": stats_cold[-1]["final_iters"],
+                           "final_learned": stats_learned[-1]["final_iters"]},
             "residual": {"dncp": s0["dncp_relres"], "final": s0["final_relres"]},
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
     if cpu:

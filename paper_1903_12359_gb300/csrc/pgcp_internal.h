@@ -98,17 +98,19 @@ struct __align__(16) Rec {
 
 // ------------------------------------------------------------------ part (device state)
 
-struct WeldPlan {             // one weld, host description (topology only)
+struct WeldPlan {             // one weld of component B onto component A, host description
     int32_t mesh;
-    int32_t piece;            // S
+    int32_t piece;            // lowest label of B
     int32_t k;                // shared edges
     int32_t closed;           // closed weld (sphere)
-    int32_t first;            // first weld of its mesh (C is a single piece)
-    std::vector<int32_t> members;   // pieces of C before the weld
-    std::vector<int64_t> a_rows;    // copy rows of a_0..a_m (C side)
-    std::vector<int64_t> b_rows;    // copy rows of b_0..b_n (S side)
+    int32_t level;            // welds of one level join disjoint components
+    int32_t a_single, b_single;     // the side is one unwelded piece (reference 0, else -1)
+    std::vector<int32_t> members;   // pieces of A (ascending)
+    std::vector<int32_t> b_members; // pieces of B (ascending)
+    std::vector<int64_t> a_rows;    // copy rows of a_0..a_m
+    std::vector<int64_t> b_rows;    // copy rows of b_0..b_n
     std::vector<int32_t> a_glob;
-    std::vector<int32_t> new_loop;  // global ids of C's loop after the weld (empty if closed)
+    std::vector<int32_t> new_loop;  // global ids of the loop of A u B (empty if closed)
 };
 
 struct MeshInfo {
@@ -156,7 +158,8 @@ struct Part {
     DBuf<double2> local;      // DNCP (local frame)
     DBuf<double2> welded;     // FP64 welded coords (boundary rows exact; interior = weld map)
     DBuf<double2> final;      // final solve
-    int32_t sphere_w_piece = -1;
+    std::vector<uint8_t> wchart;   // [K] piece held in the chart w = 1/z (sphere)
+    DBuf<uint8_t> d_wchart;
     int32_t have_local = 0, have_weld = 0, have_final = 0;
     pgcp_stats stats{};
 };

@@ -1,14 +1,18 @@
 // Host-side welding order and per-piece set-up (runs on small integer arrays).
 //
-// Welding order (the paper shows pieces joined one at a time, Fig. 7): per
-// mesh, the component C starts as its lowest-label piece; each step joins the
-// lowest-label piece S whose shared boundary with C is ONE contiguous run of
-// >= 2 edges of C's loop and which touches C nowhere else, so C u S stays a
-// disk.  On a closed surface the last piece shares its whole loop (closed
-// weld, Section 4.4.2).
+// Welding order: Algorithm 2 joins any two disks that share one boundary arc.
+// Per mesh, components start as the pieces (ordered by lowest label) and are
+// paired level by level: every unpaired component, in that order, is paired
+// with the first later unpaired one whose loop shares ONE contiguous run of
+// >= 2 edges with it and touches it nowhere else (so the union stays a disk);
+// the earlier one is A, the later one B.  A piece's boundary thus passes
+// through about log2 K welds (joining one piece at a time composes K of them,
+// and the crowded boundary loses the arc order in FP64).  On a closed surface
+// the last two components share their whole loops (closed weld, Section 4.4.2).
 //
-// Sequences: a = C's counter-clockwise loop rotated to start at the shared
-// arc, b = S's loop reversed and rotated so that b_j = a_j for j <= k.
+// Sequences: a = A's counter-clockwise loop rotated to start at the shared
+// arc, b = B's loop reversed and rotated so that b_j = a_j for j <= k; each
+// point is read from the copy in the lowest-label piece of its side.
 // Per piece: DNCP pins at loop positions 0 and floor(b/2); reference vertex =
 // first interior vertex at or after local index floor(n/2), wrapping.
 #include <cuda_runtime.h>
@@ -98,106 +102,123 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
 
     // ---- welding order, per mesh
     P.welds.clear();
+    struct Comp {
+        std::vector<int32_t> members;
+        std::vector<int32_t> loop;
+        int32_t single;
+    };
+    // copy row of each loop vertex in the lowest-label piece of `pieces` holding it
+    auto rows_of = [&](const std::vector<int32_t>& pieces, const std::vector<int32_t>& ids) {
+        std::unordered_map<int32_t, int64_t> row;
+        for (int32_t pc : pieces)
+            for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) row.emplace(P.loop_glob[t], P.loop_rows[t]);
+        std::vector<int64_t> out;
+        out.reserve(ids.size());
+        for (int32_t g : ids) out.push_back(row.at(g));
+        return out;
+    };
+    // the weld of B onto A, if their loops share one contiguous arc (or, for the
+    // closed weld, the whole loop) and touch nowhere else
+    auto pair_weld = [&](const Comp& A, const Comp& B, bool closed_final, WeldPlan& W) -> bool {
+        const std::vector<int32_t>& A_loop = A.loop;
+        const std::vector<int32_t>& B_loop = B.loop;
+        std::unordered_set<uint64_t> b_edges;
+        for (size_t t = 0; t < B_loop.size(); ++t) b_edges.insert(dkey(B_loop[t], B_loop[(t + 1) % B_loop.size()]));
+        const size_t m1 = A_loop.size();
+        std::vector<char> shared(m1);
+        bool any = false, all = true;
+        for (size_t t = 0; t < m1; ++t) {
+            shared[t] = b_edges.count(dkey(A_loop[(t + 1) % m1], A_loop[t])) ? 1 : 0;
+            any |= shared[t];
+            all &= shared[t] != 0;
+        }
+        if (!any) return false;
+        std::vector<int32_t> rb(B_loop.rbegin(), B_loop.rend());
+        W.piece = B.members.front();
+        W.members = A.members;
+        W.b_members = B.members;
+        W.a_single = A.single;
+        W.b_single = B.single;
+        if (all) {
+            if (!(closed_final && B_loop.size() == m1)) return false;
+            size_t j = std::find(rb.begin(), rb.end(), A_loop[0]) - rb.begin();
+            std::vector<int32_t> b(rb.begin() + j, rb.end());
+            b.insert(b.end(), rb.begin(), rb.begin() + j);
+            if (b != A_loop) return false;
+            W.closed = 1;
+            W.k = (int32_t)m1 - 1;
+            W.a_glob = A_loop;
+            W.new_loop.clear();
+            W.b_rows = rows_of(B.members, b);
+            return true;
+        }
+        std::vector<size_t> starts;
+        for (size_t t = 0; t < m1; ++t)
+            if (shared[t] && !shared[(t + m1 - 1) % m1]) starts.push_back(t);
+        if (starts.size() != 1) return false;
+        const size_t i0 = starts[0];
+        int32_t k = 0;
+        while (k < (int32_t)m1 && shared[(i0 + k) % m1]) ++k;
+        if (k < 2) return false;
+        std::vector<int32_t> a(A_loop.begin() + i0, A_loop.end());
+        a.insert(a.end(), A_loop.begin(), A_loop.begin() + i0);
+        std::unordered_set<int32_t> arcv(a.begin(), a.begin() + k + 1);
+        std::unordered_set<int32_t> aset(A_loop.begin(), A_loop.end());
+        for (int32_t g : B_loop)
+            if (aset.count(g) && !arcv.count(g)) return false;
+        size_t j = std::find(rb.begin(), rb.end(), a[0]) - rb.begin();
+        std::vector<int32_t> b(rb.begin() + j, rb.end());
+        b.insert(b.end(), rb.begin(), rb.begin() + j);
+        if (!std::equal(a.begin(), a.begin() + k + 1, b.begin())) return false;
+        std::vector<int32_t> nl(a.begin() + k, a.end());
+        nl.push_back(a[0]);
+        for (size_t t = b.size(); t-- > (size_t)k + 1;) nl.push_back(b[t]);
+        W.closed = 0;
+        W.k = k;
+        W.a_glob = a;
+        W.new_loop = rotate_canonical(nl);
+        W.b_rows = rows_of(B.members, b);
+        return true;
+    };
     for (size_t mi = 0; mi < P.meshes.size(); ++mi) {
         const MeshInfo& M = P.meshes[mi];
         if (M.npiece <= 1) {
             if (P.closed) fail(PGCP_E_TOPOLOGY, "a closed surface needs at least two pieces");
             continue;
         }
-        std::vector<int32_t> C_loop = loop_of(M.piece0);
-        std::vector<int32_t> members = {M.piece0};
-        std::vector<int32_t> remaining;
-        for (int32_t i = M.piece0 + 1; i < M.piece0 + M.npiece; ++i) remaining.push_back(i);
-        bool first = true;
-        while (!remaining.empty()) {
-            bool found = false;
-            WeldPlan W;
-            for (int32_t sp : remaining) {
-                std::vector<int32_t> S_loop = loop_of(sp);
-                std::unordered_set<uint64_t> s_edges;
-                for (size_t t = 0; t < S_loop.size(); ++t) s_edges.insert(dkey(S_loop[t], S_loop[(t + 1) % S_loop.size()]));
-                const size_t m1 = C_loop.size();
-                std::vector<char> shared(m1);
-                bool any = false, all = true;
-                for (size_t t = 0; t < m1; ++t) {
-                    shared[t] = s_edges.count(dkey(C_loop[(t + 1) % m1], C_loop[t])) ? 1 : 0;
-                    any |= shared[t];
-                    all &= shared[t] != 0;
-                }
-                if (!any) continue;
-                std::vector<int32_t> rb(S_loop.rbegin(), S_loop.rend());
-                if (all) {
-                    if (!(P.closed && remaining.size() == 1 && S_loop.size() == m1)) continue;
-                    size_t j = std::find(rb.begin(), rb.end(), C_loop[0]) - rb.begin();
-                    std::vector<int32_t> b(rb.begin() + j, rb.end());
-                    b.insert(b.end(), rb.begin(), rb.begin() + j);
-                    if (b != C_loop) continue;
-                    W.closed = 1;
-                    W.k = (int32_t)m1 - 1;
-                    W.a_glob = C_loop;
-                    W.b_rows.clear();
-                    W.new_loop.clear();
-                    std::vector<int32_t> bg = b;
-                    W.piece = sp;
-                    // b rows
-                    std::unordered_map<int32_t, int64_t> srow;
-                    for (int64_t t = P.loff[sp]; t < P.loff[sp + 1]; ++t) srow[P.loop_glob[t]] = P.loop_rows[t];
-                    for (int32_t g : bg) W.b_rows.push_back(srow.at(g));
-                    found = true;
+        std::vector<Comp> comps;
+        for (int32_t i = M.piece0; i < M.piece0 + M.npiece; ++i) comps.push_back(Comp{{i}, loop_of(i), 1});
+        int32_t level = 0;
+        while (comps.size() > 1) {
+            const bool final2 = P.closed && comps.size() == 2;
+            std::vector<char> used(comps.size(), 0);
+            std::vector<Comp> next;
+            for (size_t i = 0; i < comps.size(); ++i) {
+                if (used[i]) continue;
+                for (size_t j = i + 1; j < comps.size(); ++j) {
+                    if (used[j]) continue;
+                    WeldPlan W;
+                    if (!pair_weld(comps[i], comps[j], final2, W)) continue;
+                    W.mesh = (int32_t)mi;
+                    W.level = level;
+                    W.a_rows = rows_of(W.members, W.a_glob);
+                    std::vector<int32_t> mem = comps[i].members;
+                    mem.insert(mem.end(), comps[j].members.begin(), comps[j].members.end());
+                    std::sort(mem.begin(), mem.end());
+                    next.push_back(Comp{mem, W.new_loop, 0});
+                    P.welds.push_back(std::move(W));
+                    used[i] = used[j] = 1;
                     break;
                 }
-                std::vector<size_t> starts;
-                for (size_t t = 0; t < m1; ++t)
-                    if (shared[t] && !shared[(t + m1 - 1) % m1]) starts.push_back(t);
-                if (starts.size() != 1) continue;
-                size_t i0 = starts[0];
-                int32_t k = 0;
-                while (k < (int32_t)m1 && shared[(i0 + k) % m1]) ++k;
-                if (k < 2) continue;
-                std::vector<int32_t> a(C_loop.begin() + i0, C_loop.end());
-                a.insert(a.end(), C_loop.begin(), C_loop.begin() + i0);
-                std::unordered_set<int32_t> arcv(a.begin(), a.begin() + k + 1);
-                std::unordered_set<int32_t> cset(C_loop.begin(), C_loop.end());
-                bool touch = false;
-                for (int32_t g : S_loop)
-                    if (cset.count(g) && !arcv.count(g)) touch = true;
-                if (touch) continue;
-                size_t j = std::find(rb.begin(), rb.end(), a[0]) - rb.begin();
-                std::vector<int32_t> b(rb.begin() + j, rb.end());
-                b.insert(b.end(), rb.begin(), rb.begin() + j);
-                if (!std::equal(a.begin(), a.begin() + k + 1, b.begin())) continue;
-                std::vector<int32_t> nl(a.begin() + k, a.end());
-                nl.push_back(a[0]);
-                for (size_t t = b.size(); t-- > (size_t)k + 1;) nl.push_back(b[t]);
-                W.closed = 0;
-                W.k = k;
-                W.piece = sp;
-                W.a_glob = a;
-                W.new_loop = rotate_canonical(nl);
-                std::unordered_map<int32_t, int64_t> srow;
-                for (int64_t t = P.loff[sp]; t < P.loff[sp + 1]; ++t) srow[P.loop_glob[t]] = P.loop_rows[t];
-                W.b_rows.clear();
-                for (int32_t g : b) W.b_rows.push_back(srow.at(g));
-                found = true;
-                break;
             }
-            if (!found) fail(PGCP_E_SCHEDULE, "mesh " + std::to_string(mi) +
-                                                   ": no piece shares one contiguous arc with the welded component");
-            W.mesh = (int32_t)mi;
-            W.first = first ? 1 : 0;
-            W.members = members;
-            std::sort(W.members.begin(), W.members.end());
-            // a rows: copy in the lowest-label member whose loop holds the vertex
-            std::unordered_map<int32_t, int64_t> crow;
-            for (int32_t pc : W.members)
-                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) crow.emplace(P.loop_glob[t], P.loop_rows[t]);
-            W.a_rows.clear();
-            for (int32_t g : W.a_glob) W.a_rows.push_back(crow.at(g));
-            members.push_back(W.piece);
-            remaining.erase(std::find(remaining.begin(), remaining.end(), W.piece));
-            if (!W.closed) C_loop = W.new_loop;
-            P.welds.push_back(std::move(W));
-            first = false;
+            if (next.empty())
+                fail(PGCP_E_SCHEDULE, "mesh " + std::to_string(mi) + ": no two components share one contiguous arc");
+            for (size_t i = 0; i < comps.size(); ++i)
+                if (!used[i]) next.push_back(comps[i]);
+            std::sort(next.begin(), next.end(),
+                      [](const Comp& x, const Comp& y) { return x.members.front() < y.members.front(); });
+            comps.swap(next);
+            ++level;
         }
         if (P.closed && !P.welds.back().closed)
             fail(PGCP_E_SCHEDULE, "closed surface did not end with a closed weld");

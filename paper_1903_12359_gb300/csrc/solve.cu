@@ -56,7 +56,8 @@ __global__ void k_final_init(int64_t n, const uint8_t* __restrict__ is_bnd, cons
 
 // out[v] from the lowest-label copy; seam mismatch = max |copy - chosen copy|
 __global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, const int32_t* __restrict__ first_copy,
-                         const int32_t* __restrict__ row_piece, int32_t w_piece, const double2* __restrict__ X,
+                         const int32_t* __restrict__ row_piece, const uint8_t* __restrict__ wchart,
+                         const double2* __restrict__ X,
                          int dim, double* __restrict__ out, unsigned long long* __restrict__ mism) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Nc) return;
@@ -70,10 +71,10 @@ __global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, cons
             c[1] = z.y;
             c[2] = 0.0;
         } else {
-            // orientation-preserving inverse stereographic projection; the piece
-            // holding infinity is stored in the chart w = 1/z
+            // orientation-preserving inverse stereographic projection; the
+            // pieces around infinity are stored in the chart w = 1/z
             double r2 = z.x * z.x + z.y * z.y, d = 1.0 + r2;
-            if (row_piece[row] == w_piece) {
+            if (wchart[row_piece[row]]) {
                 c[0] = 2.0 * z.x / d;
                 c[1] = 2.0 * z.y / d;
                 c[2] = (1.0 - r2) / d;
@@ -159,7 +160,7 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     mism.zero();
     // vertices in no face stay NaN (all-ones bit pattern)
     PGCP_CUDA(cudaMemsetAsync(o, 0xff, dim * P.nv * sizeof(double), s));
-    { k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.sphere_w_piece, P.final.p,
+    { k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.d_wchart.p, P.final.p,
                                      dim, o, mism.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     unsigned long long m = 0;

@@ -733,8 +733,9 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
     // welds grouped by mesh, in order
     std::vector<std::vector<int>> by_mesh(nmesh);
     for (size_t w = 0; w < P.welds.size(); ++w) by_mesh[P.welds[w].mesh].push_back((int)w);
+    // one round per level: the welds of a level (of every mesh) join disjoint components
     size_t rounds = 0;
-    for (auto& v : by_mesh) rounds = std::max(rounds, v.size());
+    for (const WeldPlan& W : P.welds) rounds = std::max(rounds, (size_t)W.level + 1);
     P.welded.alloc(P.Nc, s);
     PGCP_CUDA(cudaMemcpyAsync(P.welded.p, P.local.p, P.Nc * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     // record store (sizes known from the plans)
@@ -795,8 +796,8 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
     ctx->err.zero();
     for (size_t r = 0; r < rounds; ++r) {
         std::vector<int> jobs_w;
-        for (int mi = 0; mi < nmesh; ++mi)
-            if (r < by_mesh[mi].size()) jobs_w.push_back(by_mesh[mi][r]);
+        for (size_t w = 0; w < P.welds.size(); ++w)
+            if ((size_t)P.welds[w].level == r) jobs_w.push_back((int)w);
         // ---- phase 1 inputs
         std::vector<SeqMeta> seqs;
         std::vector<JobMeta> jobs;
@@ -821,9 +822,9 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
                     xi.push_back(0);
                     xinf.push_back(0);
                 }
-                // auxiliary points: reference (C: 0 for a single piece, -1 after a
-                // weld; S: 0) and infinity
-                double ref = (side == 0 && !W.first) ? -1.0 : 0.0;
+                // auxiliary points: the side's reference (0 for a single piece,
+                // -1 for a welded component) and infinity
+                double ref = (side == 0 ? W.a_single : W.b_single) ? 0.0 : -1.0;
                 item_seq.push_back(sid); rows.push_back(-1); xr.push_back(ref); xi.push_back(0); xinf.push_back(0);
                 item_seq.push_back(sid); rows.push_back(-1); xr.push_back(0); xi.push_back(0); xinf.push_back(1);
             }
@@ -882,7 +883,7 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
                 }
             };
             for (int32_t pc : W.members) add_piece(pc, 0);
-            add_piece(W.piece, 1);
+            for (int32_t pc : W.b_members) add_piece(pc, 1);
         }
         DBuf<int32_t> d2_rows, d2_arc, d2_chain;
         upload(d2_rows, p2_rows, s);
@@ -1009,7 +1010,7 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         for (size_t w = 0; w < P.welds.size(); ++w) {
             const WeldPlan& W = P.welds[w];
             for (int32_t pc : W.members) pch[pc].push_back(2 * (int32_t)w);
-            pch[W.piece].push_back(2 * (int32_t)w + 1);
+            for (int32_t pc : W.b_members) pch[pc].push_back(2 * (int32_t)w + 1);
         }
         for (int mi = 0; mi < nmesh; ++mi)
             if (disk_chain[mi] >= 0)
@@ -1040,7 +1041,13 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         }
         PGCP_CUDA(cudaStreamSynchronize(s));
     }
-    if (P.closed && !P.welds.empty()) P.sphere_w_piece = P.welds.back().piece;
+    // sphere: the pieces of each closed weld's B side are held in the chart w = 1/z
+    P.wchart.assign(P.K, 0);
+    for (const WeldPlan& W : P.welds)
+        if (W.closed)
+            for (int32_t pc : W.b_members) P.wchart[pc] = 1;
+    upload(P.d_wchart, P.wchart, s);
+    PGCP_CUDA(cudaStreamSynchronize(s));
     P.have_weld = 1;
 }
 
