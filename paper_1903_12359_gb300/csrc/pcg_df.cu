@@ -151,11 +151,23 @@ struct RunArgs {
     int32_t max_iters;
     int32_t dncp;
     unsigned long long* work;           // [2] free rows, stored entries, summed over iterations
+    // dynamic schedule (k_pcg_dyn)
+    const DfRun* __restrict__ chunks;   // RUN_THREADS-row chunks inside pieces
+    int32_t nchunks;
+    const int32_t* __restrict__ nch;    // [nseg] chunks per piece
+    unsigned int* CTR;                  // [4] chunk counters (phase B of k: 2k % 4, phase A: 2k+1 % 4)
+    unsigned int* CNTB;                 // [2][nseg] chunks of a piece reduced in phase B
+    unsigned int* CNTA;                 // [2][nseg] ... in phase A
+    double* ALPHA;                      // [2][2 nseg]
+    double* BETA;                       // [2][2 nseg]
+    unsigned int* DONEF;                // [2 nseg] coordinate converged (monotonic)
 };
 
+// Accumulators written by other blocks (atomics, then a grid sync) are read
+// through L2 (__ldcg): another SM's L1 may hold an older line.
 __device__ __forceinline__ bool piece_done(const double* RD, const double* THR, int s, int c, bool dncp) {
-    if (dncp) return RD[2 * s] + RD[2 * s + 1] <= THR[2 * s] + THR[2 * s + 1];
-    return RD[2 * s + c] <= THR[2 * s + c];
+    if (dncp) return __ldcg(RD + 2 * s) + __ldcg(RD + 2 * s + 1) <= THR[2 * s] + THR[2 * s + 1];
+    return __ldcg(RD + 2 * s + c) <= THR[2 * s + c];
 }
 
 // Sum NV double-float values over the block on the FP32 pipe; thread 0 gets
@@ -251,11 +263,12 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
                 double b0 = 0.0, b1 = 0.0;
                 if (k > 0) {
                     if (a.dncp) {
-                        const double num = RRk[2 * s] + RRk[2 * s + 1], den = RRm[2 * s] + RRm[2 * s + 1];
+                        const double num = __ldcg(RRk + 2 * s) + __ldcg(RRk + 2 * s + 1);
+                        const double den = __ldcg(RRm + 2 * s) + __ldcg(RRm + 2 * s + 1);
                         b0 = b1 = den > 0.0 ? num / den : 0.0;
                     } else {
-                        b0 = RRm[2 * s] > 0.0 ? RRk[2 * s] / RRm[2 * s] : 0.0;
-                        b1 = RRm[2 * s + 1] > 0.0 ? RRk[2 * s + 1] / RRm[2 * s + 1] : 0.0;
+                        b0 = __ldcg(RRm + 2 * s) > 0.0 ? __ldcg(RRk + 2 * s) / __ldcg(RRm + 2 * s) : 0.0;
+                        b1 = __ldcg(RRm + 2 * s + 1) > 0.0 ? __ldcg(RRk + 2 * s + 1) / __ldcg(RRm + 2 * s + 1) : 0.0;
                     }
                 }
                 sc[slot][0] = b0;
@@ -352,11 +365,11 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
                 const bool d1 = piece_done(RDk, a.THR, s, 1, a.dncp);
                 double al0 = 0.0, al1 = 0.0;
                 if (a.dncp) {
-                    const double den = PQk[2 * s] + PQk[2 * s + 1];
-                    al0 = al1 = den > 0.0 ? (RRk[2 * s] + RRk[2 * s + 1]) / den : 0.0;
+                    const double den = __ldcg(PQk + 2 * s) + __ldcg(PQk + 2 * s + 1);
+                    al0 = al1 = den > 0.0 ? (__ldcg(RRk + 2 * s) + __ldcg(RRk + 2 * s + 1)) / den : 0.0;
                 } else {
-                    if (!d0) al0 = PQk[2 * s] > 0.0 ? RRk[2 * s] / PQk[2 * s] : 0.0;
-                    if (!d1) al1 = PQk[2 * s + 1] > 0.0 ? RRk[2 * s + 1] / PQk[2 * s + 1] : 0.0;
+                    if (!d0) al0 = __ldcg(PQk + 2 * s) > 0.0 ? __ldcg(RRk + 2 * s) / __ldcg(PQk + 2 * s) : 0.0;
+                    if (!d1) al1 = __ldcg(PQk + 2 * s + 1) > 0.0 ? __ldcg(RRk + 2 * s + 1) / __ldcg(PQk + 2 * s + 1) : 0.0;
                 }
                 sc[slot][0] = al0;
                 sc[slot][1] = al1;
@@ -407,6 +420,318 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
         if (wrows) atomicAdd(&a.work[0], wrows);
         if (wnnz) atomicAdd(&a.work[1], wnnz);
         if (blockIdx.x == 0) a.out_iters[0] = k;
+    }
+}
+
+// Dynamic schedule.  Blocks take RUN_THREADS-row chunks (inside one piece)
+// from a global counter; the next chunk's index and descriptor are fetched
+// while the current chunk runs.  Each block reduces its partial sums once per
+// piece it touched; the block that completes a piece's sum (counting chunks)
+// computes the piece's alpha (phase B) or beta and converged flags (phase A)
+// for everyone, so no block waits on scalars at a chunk start.
+template <typename A, int MINB>
+__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_dyn(RunArgs<A> a) {
+    using S = typename A::S;
+    using V = typename A::V;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float2 red[4 * (RUN_THREADS / 32)];
+    __shared__ int s_idx[3];        // chunk ring: current, next, the one after
+    __shared__ DfRun s_chunk[3];
+    const int nseg = a.nseg;
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ colp = a.col;
+    const S* __restrict__ valp = a.val;
+    const float* __restrict__ dgp = a.dgn;
+    unsigned long long wrows = 0, wnnz = 0;
+    int k = 0;
+    for (; k < a.max_iters; ++k) {
+        const double* RRk = a.RR + (k % 3) * 2 * nseg;
+        double* RRn = a.RR + ((k + 1) % 3) * 2 * nseg;
+        double* RDn = a.RD + ((k + 1) % 3) * 2 * nseg;
+        double* PQk = a.PQ + (k % 2) * 2 * nseg;
+        const double* BETk = a.BETA + (k % 2) * 2 * nseg;
+        double* BETn = a.BETA + ((k + 1) % 2) * 2 * nseg;
+        double* ALPk = a.ALPHA + (k % 2) * 2 * nseg;
+        unsigned* CB = a.CNTB + (k % 2) * nseg;
+        unsigned* CA = a.CNTA + (k % 2) * nseg;
+        // ---------------- phase B: p = r + beta p, q = A~ r + beta q, <p, q>
+        if (blockIdx.x == 0) {   // slots that this iteration's phase A and the next phase B fill
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) {
+                RRn[i] = 0.0;
+                RDn[i] = 0.0;
+            }
+            for (int i = threadIdx.x; i < nseg; i += blockDim.x) a.CNTB[((k + 1) % 2) * nseg + i] = 0u;
+            if (threadIdx.x == 0) a.CTR[(2 * k + 2) % 4] = 0u;
+        }
+        bool any = false;
+        {
+            unsigned* ctr = a.CTR + (2 * k) % 4;
+            if (threadIdx.x == 0) {
+                for (int t = 0; t < 2; ++t) {
+                    const int c = (int)atomicAdd(ctr, 1u);
+                    s_idx[t] = c;
+                    if (c < a.nchunks) s_chunk[t] = a.chunks[c];
+                }
+            }
+            __syncthreads();
+            int seg = -1, m = 0;
+            S acc0 = A::zero(), acc1 = A::zero();
+            auto flush = [&]() {
+                float2 pv[2] = {A::as_df(acc0), A::as_df(acc1)};
+                double v[2];
+                block_sum_df<2>(pv, red, v);
+                if (threadIdx.x == 0) {
+                    atomicAdd(&PQk[2 * seg], v[0]);
+                    atomicAdd(&PQk[2 * seg + 1], v[1]);
+                    __threadfence();
+                    const unsigned old = atomicAdd(&CB[seg], (unsigned)m);
+                    if (old + (unsigned)m == (unsigned)a.nch[seg]) {   // this block completed <p, q>
+                        __threadfence();
+                        const double pq0 = __ldcg(PQk + 2 * seg), pq1 = __ldcg(PQk + 2 * seg + 1);
+                        const double rr0 = __ldcg(RRk + 2 * seg), rr1 = __ldcg(RRk + 2 * seg + 1);
+                        double al0, al1;
+                        if (a.dncp) {
+                            const double den = pq0 + pq1;
+                            al0 = al1 = den > 0.0 ? (rr0 + rr1) / den : 0.0;
+                        } else {
+                            al0 = (!__ldcg(a.DONEF + 2 * seg) && pq0 > 0.0) ? rr0 / pq0 : 0.0;
+                            al1 = (!__ldcg(a.DONEF + 2 * seg + 1) && pq1 > 0.0) ? rr1 / pq1 : 0.0;
+                        }
+                        __stcg(ALPk + 2 * seg, al0);
+                        __stcg(ALPk + 2 * seg + 1, al1);
+                    }
+                }
+            };
+            // this thread's row bounds in the current chunk, loaded one chunk ahead
+            int bcur = 0, ecur = 0;
+            if (s_idx[0] < a.nchunks && s_chunk[0].lo + (int)threadIdx.x < s_chunk[0].hi) {
+                bcur = __ldg(rp + s_chunk[0].lo + threadIdx.x);
+                ecur = __ldg(rp + s_chunk[0].lo + threadIdx.x + 1);
+            }
+            for (int it = 0;; ++it) {
+                const int c = s_idx[it % 3];
+                if (c >= a.nchunks) break;
+                const DfRun ch = s_chunk[it % 3];
+                const int cn = s_idx[(it + 1) % 3];
+                int nxt = 0;
+                if (threadIdx.x == 0) nxt = (int)atomicAdd(ctr, 1u);   // two chunks ahead, in flight
+                // next chunk: this thread's row bounds, and its vectors into L2
+                int bn = 0, en = 0, nrow = -1;
+                if (cn < a.nchunks) {
+                    const DfRun chn = s_chunk[(it + 1) % 3];
+                    if (chn.lo + (int)threadIdx.x < chn.hi) {
+                        nrow = chn.lo + threadIdx.x;
+                        bn = __ldg(rp + nrow);
+                        en = __ldg(rp + nrow + 1);
+                        prefetch_l2(a.p + nrow);
+                        prefetch_l2(a.q + nrow);
+                        prefetch_l2(a.r + nrow);
+                    }
+                }
+                if (ch.seg != seg) {   // block-uniform
+                    if (seg >= 0 && m > 0) flush();
+                    seg = ch.seg;
+                    m = 0;
+                    acc0 = A::zero();
+                    acc1 = A::zero();
+                }
+                const bool d0 = __ldcg(a.DONEF + 2 * seg) != 0u, d1 = __ldcg(a.DONEF + 2 * seg + 1) != 0u;
+                if (!(d0 && d1)) {
+                    any = true;
+                    ++m;
+                    const S beta0 = A::from_d(__ldcg(BETk + 2 * seg)), beta1 = A::from_d(__ldcg(BETk + 2 * seg + 1));
+                    const int row = ch.lo + threadIdx.x;
+                    const int b = bcur, e = ecur;
+                    if (row < ch.hi && b < e) {
+                        S w0 = A::zero(), w1 = A::zero();
+                        int j = b;
+                        for (; j + 4 <= e; j += 4) {
+                            int32_t cc[4];
+                            S v[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                cc[u] = __ldg(colp + j + u);
+                                v[u] = __ldg(valp + j + u);
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) spmv_entry<A>(cc[u], v[u], a.r, w0, w1);
+                        }
+                        for (; j < e; ++j) spmv_entry<A>(__ldg(colp + j), __ldg(valp + j), a.r, w0, w1);
+                        const V rr = a.r[row];
+                        const V pp = a.p[row], qq = a.q[row];
+                        S px = A::cx(pp), py = A::cy(pp), qx = A::cx(qq), qy = A::cy(qq);
+                        if (!d0) {
+                            px = A::fma(A::cx(rr), beta0, px);
+                            qx = A::fma(w0, beta0, qx);
+                            acc0 = A::fma(acc0, px, qx);
+                        }
+                        if (!d1) {
+                            py = A::fma(A::cy(rr), beta1, py);
+                            qy = A::fma(w1, beta1, qy);
+                            acc1 = A::fma(acc1, py, qy);
+                        }
+                        a.p[row] = A::pack(px, py);
+                        a.q[row] = A::pack(qx, qy);
+                    }
+                    if (threadIdx.x == 0) {
+                        wrows += (unsigned long long)ch.frows;
+                        wnnz += (unsigned long long)ch.fnnz;
+                    }
+                }
+                if (nrow >= 0 && en > bn) {   // the next row's matrix slice into L2
+                    prefetch_l2(colp + bn);
+                    prefetch_l2(valp + bn);
+                    prefetch_l2(valp + en - 1);
+                }
+                bcur = bn;
+                ecur = en;
+                if (threadIdx.x == 0) {
+                    s_idx[(it + 2) % 3] = nxt;
+                    if (nxt < a.nchunks) s_chunk[(it + 2) % 3] = a.chunks[nxt];
+                }
+                __syncthreads();
+            }
+            if (seg >= 0 && m > 0) flush();
+        }
+        if (threadIdx.x == 0 && any) *(volatile unsigned*)&a.ACT[k % 3] = 1u;
+        grid.sync();
+        // ---------------- phase A: x~ += alpha p, r -= alpha q, norms
+        if (blockIdx.x == 0) {
+            double* z = a.PQ + ((k + 1) % 2) * 2 * nseg;
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) z[i] = 0.0;
+            for (int i = threadIdx.x; i < nseg; i += blockDim.x) a.CNTA[((k + 1) % 2) * nseg + i] = 0u;
+            if (threadIdx.x == 0) {
+                a.ACT[(k + 1) % 3] = 0;
+                a.CTR[(2 * k + 3) % 4] = 0u;
+            }
+        }
+        {
+            unsigned* ctr = a.CTR + (2 * k + 1) % 4;
+            if (threadIdx.x == 0) {
+                for (int t = 0; t < 2; ++t) {
+                    const int c = (int)atomicAdd(ctr, 1u);
+                    s_idx[t] = c;
+                    if (c < a.nchunks) s_chunk[t] = a.chunks[c];
+                }
+            }
+            __syncthreads();
+            int seg = -1, m = 0;
+            S rr0 = A::zero(), rr1 = A::zero();
+            float rd0 = 0.f, rd1 = 0.f;
+            auto flush = [&]() {
+                float2 pv[4] = {A::as_df(rr0), A::as_df(rr1), make_float2(rd0, 0.f), make_float2(rd1, 0.f)};
+                double v[4];
+                block_sum_df<4>(pv, red, v);
+                if (threadIdx.x == 0) {
+                    atomicAdd(&RRn[2 * seg], v[0]);
+                    atomicAdd(&RRn[2 * seg + 1], v[1]);
+                    atomicAdd(&RDn[2 * seg], v[2]);
+                    atomicAdd(&RDn[2 * seg + 1], v[3]);
+                    __threadfence();
+                    const unsigned old = atomicAdd(&CA[seg], (unsigned)m);
+                    if (old + (unsigned)m == (unsigned)a.nch[seg]) {   // this block completed the norms
+                        __threadfence();
+                        const double n0 = __ldcg(RRn + 2 * seg), n1 = __ldcg(RRn + 2 * seg + 1);
+                        const double o0 = __ldcg(RRk + 2 * seg), o1 = __ldcg(RRk + 2 * seg + 1);
+                        const double e0 = __ldcg(RDn + 2 * seg), e1 = __ldcg(RDn + 2 * seg + 1);
+                        const double t0 = a.THR[2 * seg], t1 = a.THR[2 * seg + 1];
+                        if (a.dncp) {
+                            const double bt = (o0 + o1) > 0.0 ? (n0 + n1) / (o0 + o1) : 0.0;
+                            __stcg(BETn + 2 * seg, bt);
+                            __stcg(BETn + 2 * seg + 1, bt);
+                            if (e0 + e1 <= t0 + t1) {
+                                __stcg(a.DONEF + 2 * seg, 1u);
+                                __stcg(a.DONEF + 2 * seg + 1, 1u);
+                            }
+                        } else {
+                            __stcg(BETn + 2 * seg, o0 > 0.0 ? n0 / o0 : 0.0);
+                            __stcg(BETn + 2 * seg + 1, o1 > 0.0 ? n1 / o1 : 0.0);
+                            if (e0 <= t0) __stcg(a.DONEF + 2 * seg, 1u);
+                            if (e1 <= t1) __stcg(a.DONEF + 2 * seg + 1, 1u);
+                        }
+                    }
+                }
+            };
+            for (int it = 0;; ++it) {
+                const int c = s_idx[it % 3];
+                if (c >= a.nchunks) break;
+                const DfRun ch = s_chunk[it % 3];
+                const int cn = s_idx[(it + 1) % 3];
+                int nxt = 0;
+                if (threadIdx.x == 0) nxt = (int)atomicAdd(ctr, 1u);
+                if (cn < a.nchunks) {   // next chunk's row streams into L2
+                    const DfRun chn = s_chunk[(it + 1) % 3];
+                    const int nrow = chn.lo + threadIdx.x;
+                    if (nrow < chn.hi) {
+                        prefetch_l2(a.x + nrow);
+                        prefetch_l2(a.r + nrow);
+                        prefetch_l2(a.p + nrow);
+                        prefetch_l2(a.q + nrow);
+                    }
+                }
+                if (ch.seg != seg) {
+                    if (seg >= 0 && m > 0) flush();
+                    seg = ch.seg;
+                    m = 0;
+                    rr0 = A::zero();
+                    rr1 = A::zero();
+                    rd0 = rd1 = 0.f;
+                }
+                const bool d0 = __ldcg(a.DONEF + 2 * seg) != 0u, d1 = __ldcg(a.DONEF + 2 * seg + 1) != 0u;
+                if (!(d0 && d1)) {
+                    ++m;
+                    const S al0 = A::from_d(__ldcg(ALPk + 2 * seg)), al1 = A::from_d(__ldcg(ALPk + 2 * seg + 1));
+                    const int row = ch.lo + threadIdx.x;
+                    if (row < ch.hi) {
+                        const float d = __ldg(dgp + row);
+                        if (d != 0.f) {
+                            const V xx = a.x[row], rv = a.r[row];
+                            const V pp = a.p[row], qq = a.q[row];
+                            const S x0 = A::fma(A::cx(xx), al0, A::cx(pp)), x1 = A::fma(A::cy(xx), al1, A::cy(pp));
+                            const S r0 = A::fma(A::cx(rv), A::neg(al0), A::cx(qq));
+                            const S r1 = A::fma(A::cy(rv), A::neg(al1), A::cy(qq));
+                            a.x[row] = A::pack(x0, x1);
+                            a.r[row] = A::pack(r0, r1);
+                            rr0 = A::fma(rr0, r0, r0);
+                            rr1 = A::fma(rr1, r1, r1);
+                            const float l0 = A::lead(r0), l1 = A::lead(r1);
+                            rd0 = fmaf(d * l0, l0, rd0);
+                            rd1 = fmaf(d * l1, l1, rd1);
+                        }
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    s_idx[(it + 2) % 3] = nxt;
+                    if (nxt < a.nchunks) s_chunk[(it + 2) % 3] = a.chunks[nxt];
+                }
+                __syncthreads();
+            }
+            if (seg >= 0 && m > 0) flush();
+        }
+        grid.sync();
+        if (*(volatile unsigned*)&a.ACT[k % 3] == 0u) break;
+    }
+    if (threadIdx.x == 0) {
+        if (wrows) atomicAdd(&a.work[0], wrows);
+        if (wnnz) atomicAdd(&a.work[1], wnnz);
+        if (blockIdx.x == 0) a.out_iters[0] = k;
+    }
+}
+
+// Initial state of the dynamic schedule: converged flags from <r0, r0>, beta 0.
+__global__ void k_dyn_init(int nseg, int dncp, const double* __restrict__ RD0, const double* __restrict__ THR,
+                           unsigned int* __restrict__ DONEF, double* __restrict__ BETA0) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    BETA0[2 * s] = 0.0;
+    BETA0[2 * s + 1] = 0.0;
+    if (dncp) {
+        const unsigned d = RD0[2 * s] + RD0[2 * s + 1] <= THR[2 * s] + THR[2 * s + 1] ? 1u : 0u;
+        DONEF[2 * s] = d;
+        DONEF[2 * s + 1] = d;
+    } else {
+        DONEF[2 * s] = RD0[2 * s] <= THR[2 * s] ? 1u : 0u;
+        DONEF[2 * s + 1] = RD0[2 * s + 1] <= THR[2 * s + 1] ? 1u : 0u;
     }
 }
 
@@ -582,6 +907,11 @@ void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSyste
     PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RUN_THREADS, 0));
     if (per_sm <= 0) fail(PGCP_E_CUDA, "run-based PCG kernel cannot be resident");
     D.per_sm = per_sm;
+    int per_sm_dyn = 0;
+    const void* kd = D.minb == 3 ? (const void*)k_pcg_dyn<A, 3> : (const void*)k_pcg_dyn<A, 4>;
+    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dyn, kd, RUN_THREADS, 0));
+    if (per_sm_dyn <= 0) fail(PGCP_E_CUDA, "dynamically scheduled PCG kernel cannot be resident");
+    D.dyn_grid = per_sm_dyn * ctx->num_sms;
     const size_t vb = sizeof(typename A::V);
     D.x.alloc(n * vb, s);
     D.r.alloc(n * vb, s);
@@ -600,13 +930,36 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, D.RR.p,
                                                             D.RD.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
+    if (D.dyn) {
+        { k_dyn_init<<<(unsigned)std::max<int64_t>(1, ceil_div((int64_t)P.K, 256)), 256, 0, s>>>(
+            P.K, D.dncp, D.RD.p, D.THR.p, D.DONEF.p, D.BETA.p); ::pgcp::note_launch(); }
+        D.CTR.zero();
+        D.CNTB.zero();
+        D.CNTA.zero();
+        PGCP_CUDA(cudaGetLastError());
+    }
     PGCP_CUDA(cudaEventRecord(e0, s));
     RunArgs<A> a{(int32_t)D.n, P.K, D.rp.p, D.col.p, reinterpret_cast<const typename A::S*>(D.val.p), D.dgn.p, xv, rv,
                  pv, qv, D.runs.p, D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, max_iters,
                  D.dncp, D.work.p};
+    a.chunks = D.chunks.p;
+    a.nchunks = D.nchunks;
+    a.nch = D.nch.p;
+    a.CTR = D.CTR.p;
+    a.CNTB = D.CNTB.p;
+    a.CNTA = D.CNTA.p;
+    a.ALPHA = D.ALPHA.p;
+    a.BETA = D.BETA.p;
+    a.DONEF = D.DONEF.p;
     void* args[] = {(void*)&a};
-    const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
-    { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(D.grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    if (D.dyn) {
+        const void* kern = D.minb == 3 ? (const void*)k_pcg_dyn<A, 3> : (const void*)k_pcg_dyn<A, 4>;
+        const int grid = std::max(1, std::min(D.dyn_grid, D.nchunks));
+        { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    } else {
+        const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
+        { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(D.grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    }
 }
 
 template <typename A>
@@ -630,6 +983,9 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     const int bps = ctx->opt.pcg_blocks_per_sm;
     if (bps != 0 && bps != 3 && bps != 4) fail(PGCP_E_ARG, "pcg_blocks_per_sm must be 0, 3 or 4");
     D.minb = bps == 3 ? 3 : 4;
+    const int sched = ctx->opt.pcg_schedule;
+    if (sched < 0 || sched > 2) fail(PGCP_E_ARG, "pcg_schedule must be 0, 1 or 2");
+    D.dyn = sched == 2;
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;
     cnt.alloc(n, s);
@@ -671,6 +1027,34 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
         { k_run_stats<<<(unsigned)D.nruns, 256, 0, s>>>(D.runs.p, D.rp.p); ::pgcp::note_launch(); }
     }
     const int S = P.K;
+    // chunks of RUN_THREADS rows inside each piece (dynamic schedule)
+    {
+        std::vector<DfRun> ch;
+        std::vector<int32_t> nch(S, 0);
+        for (int i = 0; i < S; ++i)
+            for (int64_t lo = P.voff[i]; lo < P.voff[i + 1]; lo += RUN_THREADS) {
+                ch.push_back(DfRun{i, (int32_t)lo, (int32_t)std::min<int64_t>(lo + RUN_THREADS, P.voff[i + 1]), 0, 0,
+                                   0, 0, 0});
+                nch[i] += 1;
+            }
+        D.nchunks = (int32_t)ch.size();
+        D.chunks.alloc(std::max<int64_t>(1, D.nchunks), s);
+        D.nch.alloc(std::max(1, S), s);
+        PGCP_CUDA(cudaMemcpyAsync(D.chunks.p, ch.data(), ch.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
+        PGCP_CUDA(cudaMemcpyAsync(D.nch.p, nch.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (D.nchunks > 0) {
+            { k_run_stats<<<(unsigned)D.nchunks, 256, 0, s>>>(D.chunks.p, D.rp.p); ::pgcp::note_launch(); }
+        }
+        D.CTR.alloc(4, s);
+        D.CNTB.alloc(2 * S, s);
+        D.CNTA.alloc(2 * S, s);
+        D.DONEF.alloc(2 * S, s);
+        D.ALPHA.alloc(2 * 2 * S, s);
+        D.BETA.alloc(2 * 2 * S, s);
+        D.ALPHA.zero();
+        D.BETA.zero();
+        PGCP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    }
     D.RR.alloc(3 * 2 * S, s);
     D.RD.alloc(3 * 2 * S, s);
     D.PQ.alloc(2 * 2 * S, s);

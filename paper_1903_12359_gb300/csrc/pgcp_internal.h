@@ -236,6 +236,13 @@ struct DfSystem {
     DBuf<unsigned int> ACT;
     DBuf<int32_t> out_it;
     DBuf<unsigned long long> work;
+    // dynamic schedule: chunks inside pieces, per-piece chunk counts, counters
+    int dyn = 1, dyn_grid = 0;
+    int32_t nchunks = 0;
+    DBuf<DfRun> chunks;
+    DBuf<int32_t> nch;
+    DBuf<unsigned int> CTR, CNTB, CNTA, DONEF;
+    DBuf<double> ALPHA, BETA;
 };
 void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D);
 // One inner solve of A d = r64 (thresholds on the unscaled <r, r> per piece

@@ -22,6 +22,7 @@ def main(argv=None):
     ap.add_argument("--max-iters", type=int, default=300)
     ap.add_argument("--local-precision", type=int, default=2, help="0 FP64 PCG, 2 double-float PCG")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="mixed-precision PCG kernel variant: 3 or 4")
+    ap.add_argument("--schedule", type=int, default=0, help="mixed-precision PCG schedule: 1 static, 2 dynamic")
     a = ap.parse_args(argv)
     import torch
     from paper_1903_12359_gb300 import api, build, meshgen
@@ -33,7 +34,7 @@ def main(argv=None):
     if a.case == "dncp":
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, max_iters=a.max_iters,
                           max_refine=1, local_precision=a.local_precision,
-                          pcg_blocks_per_sm=a.blocks_per_sm)
+                          pcg_blocks_per_sm=a.blocks_per_sm, pcg_schedule=a.schedule)
         part = ctx.partition(V, F, face_labels=L)
         try:
             part.local_param()
@@ -49,7 +50,8 @@ def main(argv=None):
                           "pcg_launches": st["pcg_launches"]}))
     else:
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10,
-                          local_precision=a.local_precision, pcg_blocks_per_sm=a.blocks_per_sm)
+                          local_precision=a.local_precision, pcg_blocks_per_sm=a.blocks_per_sm,
+                          pcg_schedule=a.schedule)
         part = ctx.partition(V, F, face_labels=L)
         part.local_param()
         part.weld()
