@@ -55,10 +55,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1903_12359_gb300 import dist as pd
+    return pd.env()
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -263,9 +261,8 @@ def main():
         launches = api.launch_count() - l0
         clocks = sampler.stop(getattr(torch.cuda.get_device_properties(local), "pci_bus_id", None)) if sampler else None
         if ws > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+            from paper_1903_12359_gb300 import dist as pd
+            ms = pd.max_over_ranks(ms, device="cuda")
         return ms, stats, launches, clocks
 
     ctx = make_ctx(api.WARM_WELDMAP)
@@ -302,9 +299,8 @@ def main():
         ems = e0.elapsed_time(e1)
         wall = time.perf_counter() - t0
         if ws > 1:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
+            from paper_1903_12359_gb300 import dist as pd
+            ems = pd.max_over_ranks(ems, device="cuda")
         e2e = {"value": ws * m.nv * args.steps / (ems / 1000.0), "unit": "vertices/s",
                "h2d_bytes_per_step": int(Vh.nbytes + Fh.nbytes + Lh.nbytes),
                "d2h_bytes_per_step": int(m.nv * 2 * 8), "wall_s": wall}

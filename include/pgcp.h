@@ -249,6 +249,30 @@ pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* 
                      int32_t host_ptrs, double* out, pgcp_stats* st);
 
 /*
+ * Per-mesh status of a batch (host int32 [n_mesh], n_mesh from pgcp_part_info;
+ * library plumbing, no counterpart in the paper).  A mesh of a batch whose
+ * welding leaves its domain (PGCP_E_NUMERIC: a zipper point left the right
+ * half-plane, or the arc lost its order in FP64) is dropped: its output
+ * vertices are NaN and the other meshes complete, so pgcp_weld and
+ * pgcp_global_solve return PGCP_OK.  A single mesh, or a batch in which every
+ * mesh fails, returns the error instead.
+ */
+pgcp_status pgcp_part_mesh_status(const pgcp_part* part, int32_t* status);
+
+/*
+ * Autotuner of the batched PCG schedule (no counterpart in the paper).  Times
+ * probe_iters (>= 10) capped DNCP iterations of `part` for each candidate and
+ * stores the fastest in the context options (and in *chosen):
+ *   mixed-precision local solves: pcg_blocks_per_sm in {3, 4} x pcg_schedule
+ *   in {static, dynamic};  FP64 local solves: spmv_lanes in {1, 2, 4} x
+ *   block_rows_log2 in {8, 9, 10}.
+ * The probes overwrite the part's local map: call pgcp_local_param afterwards.
+ * ms_per_iter (may be NULL): the winner's kernel time per iteration.
+ */
+pgcp_status pgcp_autotune(pgcp_ctx* ctx, pgcp_part* part, int32_t probe_iters, pgcp_options* chosen,
+                          double* ms_per_iter);
+
+/*
  * Learned warm start (no counterpart in the paper).  A message-passing network
  * over each piece's mesh graph predicts the correction from the weld-map
  * start u_w to the final map; the final solve (Section 4.5) starts from

@@ -94,6 +94,8 @@ SIGNATURES = {
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
     "pgcp_selftest_scan": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgcp_selftest_gemm_bf16": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]),
+    "pgcp_autotune": (C.c_int, [_P, _P, C.c_int32, C.POINTER(Options), C.POINTER(C.c_double)]),
+    "pgcp_part_mesh_status": (C.c_int, [_P, _P]),
     "pgcp_gnn_num_params": (C.c_int64, []),
     "pgcp_gnn_create": (C.c_int, [_P, _P, C.POINTER(C.c_void_p)]),
     "pgcp_gnn_load": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_void_p)]),
@@ -182,6 +184,16 @@ class Context:
         self.check(load().pgcp_selftest_gemm_bf16(self.h, epilogue, N, K, _ptr(A.contiguous()), _ptr(Bt.contiguous()),
                                                   M, _ptr(bias), _ptr(C_)))
         return C_
+
+    def autotune(self, part, probe_iters: int = 200):
+        """Pick the fastest PCG schedule on `part` (pgcp_autotune); returns
+        (chosen options as a dict of the tuned fields, ms per iteration)."""
+        o = Options()
+        ms = C.c_double()
+        self.check(load().pgcp_autotune(self.h, part.h, probe_iters, C.byref(o), C.byref(ms)))
+        self.options = o
+        keys = ("pcg_blocks_per_sm", "pcg_schedule", "spmv_lanes", "block_rows_log2")
+        return {k: getattr(o, k) for k in keys}, ms.value
 
     def set_gnn(self, gnn):
         """Network for warm_start = WARM_LEARNED (None detaches)."""
@@ -275,6 +287,13 @@ class Part:
                                              C.byref(nw), C.byref(nm)))
         return {"K": K.value, "n_copies": nc.value, "nnz": nnz.value, "n_loop": nl.value, "n_welds": nw.value,
                 "n_mesh": nm.value}
+
+    def mesh_status(self):
+        """Per-mesh status codes of a batch (names from STATUS)."""
+        n = self.info()["n_mesh"]
+        st = (C.c_int32 * n)()
+        load().pgcp_part_mesh_status(self.h, st)
+        return [STATUS.get(v, str(v)) for v in st]
 
     def get_stats(self):
         st = Stats()

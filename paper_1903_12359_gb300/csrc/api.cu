@@ -438,6 +438,76 @@ pgcp_status pgcp_selftest_scan(pgcp_ctx* ctx, const int32_t* in, int64_t* out, i
     });
 }
 
+pgcp_status pgcp_autotune(pgcp_ctx* ctx, pgcp_part* part, int32_t probe_iters, pgcp_options* chosen,
+                          double* ms_per_iter) {
+    return guard(ctx, [&] {
+        if (!ctx || !part || !chosen) fail(PGCP_E_ARG, "null argument");
+        if (probe_iters < 10) fail(PGCP_E_ARG, "probe_iters must be at least 10");
+        Part& P = part->p;
+        if (!P.row_ptr.p) {
+            Timer t(ctx->stream);
+            assemble_laplacian(ctx, P);
+            P.stats.ms_assembly = t.stop();
+            P.stats.nnz = P.nnz;
+        }
+        const pgcp_options saved = ctx->opt;
+        struct Cand {
+            int bps, sched, lanes, rows;
+        };
+        std::vector<Cand> cands;
+        if (saved.local_precision == PGCP_FP64) {
+            for (int lanes : {1, 2, 4})
+                for (int rows : {8, 9, 10}) cands.push_back(Cand{saved.pcg_blocks_per_sm, saved.pcg_schedule, lanes, rows});
+        } else {
+            for (int sched : {1, 2})
+                for (int bps : {3, 4}) cands.push_back(Cand{bps, sched, saved.spmv_lanes, saved.block_rows_log2});
+        }
+        double best = INFINITY;
+        Cand pick = cands[0];
+        try {
+            for (const Cand& c : cands) {
+                ctx->opt.pcg_blocks_per_sm = c.bps;
+                ctx->opt.pcg_schedule = c.sched;
+                ctx->opt.spmv_lanes = c.lanes;
+                ctx->opt.block_rows_log2 = c.rows;
+                ctx->opt.max_iters = probe_iters;
+                ctx->opt.max_refine = 1;
+                const double ms0 = P.stats.pcg_ms;
+                try {
+                    solve_dncp(ctx, P);
+                } catch (const Thrown& t) {
+                    if (t.code != PGCP_E_NO_CONVERGENCE) throw;   // capped probe: expected
+                }
+                const int it = std::max(1, P.stats.dncp_iters);
+                const double per = (P.stats.pcg_ms - ms0) / it;
+                if (per < best) {
+                    best = per;
+                    pick = c;
+                }
+            }
+        } catch (...) {
+            ctx->opt = saved;
+            throw;
+        }
+        ctx->opt = saved;
+        ctx->opt.pcg_blocks_per_sm = pick.bps;
+        ctx->opt.pcg_schedule = pick.sched;
+        ctx->opt.spmv_lanes = pick.lanes;
+        ctx->opt.block_rows_log2 = pick.rows;
+        P.have_local = 0;   // the probes leave no usable local map
+        *chosen = ctx->opt;
+        if (ms_per_iter) *ms_per_iter = best;
+    });
+}
+
+pgcp_status pgcp_part_mesh_status(const pgcp_part* part, int32_t* status) {
+    if (!part || !status) return PGCP_E_ARG;
+    const Part& P = part->p;
+    for (size_t mi = 0; mi < P.meshes.size(); ++mi)
+        status[mi] = mi < P.mesh_status.size() ? P.mesh_status[mi] : (int32_t)PGCP_OK;
+    return PGCP_OK;
+}
+
 int64_t pgcp_gnn_num_params(void) { return gnn_num_params(); }
 
 pgcp_status pgcp_gnn_create(pgcp_ctx* ctx, const float* params, pgcp_gnn** out) {

@@ -159,6 +159,7 @@ struct Part {
     DBuf<double2> welded;     // FP64 welded coords (boundary rows exact; interior = weld map)
     DBuf<double2> final;      // final solve
     std::vector<uint8_t> wchart;   // [K] piece held in the chart w = 1/z (sphere)
+    std::vector<int32_t> mesh_status;   // [meshes] PGCP_OK, or PGCP_E_NUMERIC for a dropped mesh of a batch
     DBuf<uint8_t> d_wchart;
     int32_t have_local = 0, have_weld = 0, have_final = 0;
     pgcp_stats stats{};

@@ -61,6 +61,7 @@ __global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, cons
                          int dim, double* __restrict__ out, unsigned long long* __restrict__ mism) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Nc) return;
+    if (wchart[row_piece[i]] == 2) return;   // piece of a mesh dropped from the batch
     const int v = copy_vert[i];
     const int f = first_copy[v];
     double a[3], b[3];
@@ -74,7 +75,7 @@ __global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, cons
             // orientation-preserving inverse stereographic projection; the
             // pieces around infinity are stored in the chart w = 1/z
             double r2 = z.x * z.x + z.y * z.y, d = 1.0 + r2;
-            if (wchart[row_piece[row]]) {
+            if (wchart[row_piece[row]] == 1) {
                 c[0] = 2.0 * z.x / d;
                 c[1] = 2.0 * z.y / d;
                 c[2] = (1.0 - r2) / d;
@@ -163,6 +164,10 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     { k_gather<<<nblk(n), 256, 0, s>>>(n, P.copy_vert.p, P.first_copy.p, P.row_piece.p, P.d_wchart.p, P.final.p,
                                      dim, o, mism.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
+    // meshes dropped from a batch by the welding: NaN output
+    for (size_t mi = 0; mi < P.mesh_status.size(); ++mi)
+        if (P.mesh_status[mi] != PGCP_OK)
+            PGCP_CUDA(cudaMemsetAsync(o + dim * P.meshes[mi].v0, 0xff, dim * P.meshes[mi].nv * sizeof(double), s));
     unsigned long long m = 0;
     PGCP_CUDA(cudaMemcpyAsync(&m, mism.p, sizeof(m), cudaMemcpyDeviceToHost, s));
     if (host_out)

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -305,6 +306,7 @@ struct Phase1Args {
     double2* arcB;
     uint32_t* err;
     int32_t* fail_job;    // first failing job (for the message)
+    int32_t* job_fail;    // [jobs] 1 if the job left its domain
 };
 
 __device__ __forceinline__ Pt ldp(const Phase1Args& a, int64_t i) { return Pt{a.pr[i], a.pi[i], a.pinf[i]}; }
@@ -402,6 +404,7 @@ __global__ void __launch_bounds__(P1_THREADS) k_weld_phase1(Phase1Args a) {
             if (act && !ok) {
                 atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
                 atomicMin(a.fail_job, a.seqs[s].job);
+                atomicOr(&a.job_fail[a.seqs[s].job], 1);
             }
             // the block owning the first point of the sequence stores the record
             const SeqMeta m = a.seqs[s];
@@ -431,7 +434,10 @@ __global__ void __launch_bounds__(P1_THREADS) k_weld_phase1(Phase1Args a) {
                     const JobMeta J = a.jobs[m.job];
                     double2* dst = (m.side == 0 ? a.arcA : a.arcB) + J.arc_off + l;
                     *dst = make_double2(o.r, o.i);
-                    if (o.inf) atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
+                    if (o.inf) {
+                        atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
+                        atomicOr(&a.job_fail[m.job], 1);
+                    }
                 }
                 continue;
             }
@@ -462,6 +468,7 @@ struct DiskArgs {
     int32_t nmax;
     Rec* recs;
     uint32_t* err;
+    int32_t* seq_fail;    // [nseq] 1 if the sequence left its domain
 };
 
 __device__ bool disk_record(const DiskArgs& a, int s, int step, Rec& R, bool& ok) {
@@ -520,7 +527,10 @@ __global__ void __launch_bounds__(P1_THREADS) k_disk_phase1(DiskArgs a) {
             bool act = disk_record(a, s, step, R, ok);
             sact[threadIdx.x] = act;
             srec[threadIdx.x] = R;
-            if (act && !ok) atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
+            if (act && !ok) {
+                atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
+                atomicOr(&a.seq_fail[s], 1);
+            }
             const DiskMeta m = a.seqs[s];
             if (act && m.off >= lo && m.off < hi) a.recs[m.rec + step] = R;
         }
@@ -794,10 +804,38 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
     DBuf<ChainRef> d_chains;
     upload(d_chains, chains, s);
     ctx->err.zero();
+    // A mesh of a batch whose welding leaves its domain is dropped (status
+    // NUMERIC, output NaN) and the others go on; a single mesh fails the call.
+    std::vector<uint8_t> mfail(nmesh, 0);
+    auto mesh_failed = [&](int mi, const std::string& why) {
+        if (nmesh == 1) fail(PGCP_E_NUMERIC, why);
+        mfail[mi] = 1;
+    };
+    // meshes with a non-finite welded boundary value (only looked at after the flag)
+    auto check_finite = [&](const std::string& why) {
+        if (!(read_errors(ctx) & DE_NUMERIC)) return;
+        if (nmesh == 1) fail(PGCP_E_NUMERIC, why);
+        std::vector<double2> hw(P.Nc);
+        PGCP_CUDA(cudaMemcpyAsync(hw.data(), P.welded.p, P.Nc * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        PGCP_CUDA(cudaStreamSynchronize(s));
+        for (int mi = 0; mi < nmesh; ++mi) {
+            const MeshInfo& M = P.meshes[mi];
+            for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece && !mfail[mi]; ++pc)
+                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) {
+                    const double2 z = hw[P.loop_rows[t]];
+                    if (!std::isfinite(z.x) || !std::isfinite(z.y)) {
+                        mfail[mi] = 1;
+                        break;
+                    }
+                }
+        }
+        ctx->err.zero();
+    };
     for (size_t r = 0; r < rounds; ++r) {
         std::vector<int> jobs_w;
         for (size_t w = 0; w < P.welds.size(); ++w)
-            if ((size_t)P.welds[w].level == r) jobs_w.push_back((int)w);
+            if ((size_t)P.welds[w].level == r && !mfail[P.welds[w].mesh]) jobs_w.push_back((int)w);
+        if (jobs_w.empty()) continue;
         // ---- phase 1 inputs
         std::vector<SeqMeta> seqs;
         std::vector<JobMeta> jobs;
@@ -850,8 +888,11 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         PGCP_CUDA(cudaGetLastError());
         const int32_t big = 1 << 30;
         PGCP_CUDA(cudaMemcpyAsync(fail_job.p, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        DBuf<int32_t> job_fail;
+        job_fail.alloc(jobs.size(), s);
+        job_fail.zero();
         Phase1Args a{d_pr.p, d_pi.p, d_pinf.p, npts, d_item_seq.p, d_seqs.p, (int32_t)seqs.size(), d_jobs.p, kmax,
-                     recs.p, arcA.p, arcB.p, ctx->err.p, fail_job.p};
+                     recs.p, arcA.p, arcB.p, ctx->err.p, fail_job.p, job_fail.p};
         // few points per block: the FP64 work of a step is spread over many SMs;
         // at most P1_MAXSEQ sequences may meet in one block
         int grid = coop_grid(ctx, (const void*)k_weld_phase1, P1_THREADS, npts, 16);
@@ -861,16 +902,20 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         PGCP_CUDA(cudaGetLastError());
         uint32_t e = read_errors(ctx);
         if (e & DE_WELD_DOMAIN) {
-            int fj = 0;
-            PGCP_CUDA(cudaMemcpy(&fj, fail_job.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
-            int w = fj < (int)jobs_w.size() ? jobs_w[fj] : -1;
-            fail(PGCP_E_NUMERIC, "welding step out of its domain (weld " + std::to_string(w) +
-                                     "): a zipper point left the right half-plane or the arc lost its order");
+            std::vector<int32_t> jf(jobs.size());
+            PGCP_CUDA(cudaMemcpy(jf.data(), job_fail.p, jf.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            for (size_t jj = 0; jj < jf.size(); ++jj)
+                if (jf[jj])
+                    mesh_failed(P.welds[jobs_w[jj]].mesh,
+                                "welding step out of its domain (weld " + std::to_string(jobs_w[jj]) +
+                                    "): a zipper point left the right half-plane or the arc lost its order");
+            ctx->err.zero();
         }
         // ---- phase 2 (boundary loops of the pieces involved)
         std::vector<int32_t> p2_rows, p2_arc, p2_chain;
         for (int wi : jobs_w) {
             const WeldPlan& W = P.welds[wi];
+            if (mfail[W.mesh]) continue;
             const JobMeta& J = all_jobs[wi];
             std::unordered_map<int32_t, int> arcpos;
             for (int l = 0; l <= W.k; ++l) arcpos[W.a_glob[l]] = l;
@@ -914,7 +959,7 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             PGCP_CUDA(cudaStreamSynchronize(s));
         }
     }
-    if (read_errors(ctx) & DE_NUMERIC) fail(PGCP_E_NUMERIC, "a welded boundary point is not finite");
+    check_finite("a welded boundary point is not finite");
     // ---- disk constraint
     if (o.variant == PGCP_DISK) {
         std::vector<DiskMeta> seqs;
@@ -956,19 +1001,28 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         d_pinf.alloc(npts, s);
         { k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
                                                    d_pi.p, d_pinf.p); ::pgcp::note_launch(); }
+        DBuf<int32_t> seq_fail;
+        seq_fail.alloc(seqs.size(), s);
+        seq_fail.zero();
         DiskArgs a{d_pr.p, d_pi.p, d_pinf.p, npts, d_item_seq.p, d_seqs.p, (int32_t)seqs.size(), nmax, recs.p,
-                   ctx->err.p};
+                   ctx->err.p, seq_fail.p};
         int grid = coop_grid(ctx, (const void*)k_disk_phase1, P1_THREADS, npts, 16);
         check_block_sequences(item_seq, grid);
         void* args[] = {(void*)&a};
         { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_disk_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s)); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
-        if (read_errors(ctx) & DE_WELD_DOMAIN)
-            fail(PGCP_E_NUMERIC, "disk map: a zipper point left the right half-plane");
+        if (read_errors(ctx) & DE_WELD_DOMAIN) {
+            std::vector<int32_t> sf(seqs.size());
+            PGCP_CUDA(cudaMemcpy(sf.data(), seq_fail.p, sf.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            for (int mi = 0; mi < nmesh; ++mi)
+                if (sf[mi]) mesh_failed(mi, "disk map: a zipper point left the right half-plane");
+            ctx->err.zero();
+        }
         // images of the global boundary (sequence points 0..n) -> every copy
         std::vector<int32_t> p2_rows, p2_arc, p2_chain;
         std::vector<double2> dummy;
         for (int mi = 0; mi < nmesh; ++mi) {
+            if (mfail[mi]) continue;
             const MeshInfo& M = P.meshes[mi];
             std::unordered_map<int32_t, int> bpos;
             for (size_t l = 0; l < disk_loop[mi].size(); ++l) bpos[disk_loop[mi][l]] = (int)l;
@@ -1002,18 +1056,19 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             PGCP_CUDA(cudaGetLastError());
             PGCP_CUDA(cudaStreamSynchronize(s));
         }
-        if (read_errors(ctx) & DE_NUMERIC) fail(PGCP_E_NUMERIC, "a disk-mapped boundary point is not finite");
+        check_finite("a disk-mapped boundary point is not finite");
     }
     // ---- interior weld map: every chain of each piece, in order
     {
         std::vector<std::vector<int32_t>> pch(P.K);
         for (size_t w = 0; w < P.welds.size(); ++w) {
             const WeldPlan& W = P.welds[w];
+            if (mfail[W.mesh]) continue;
             for (int32_t pc : W.members) pch[pc].push_back(2 * (int32_t)w);
             for (int32_t pc : W.b_members) pch[pc].push_back(2 * (int32_t)w + 1);
         }
         for (int mi = 0; mi < nmesh; ++mi)
-            if (disk_chain[mi] >= 0)
+            if (disk_chain[mi] >= 0 && !mfail[mi])
                 for (int32_t pc = P.meshes[mi].piece0; pc < P.meshes[mi].piece0 + P.meshes[mi].npiece; ++pc)
                     pch[pc].push_back(disk_chain[mi]);
         std::vector<int64_t> off(P.K + 1, 0);
@@ -1048,6 +1103,28 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             for (int32_t pc : W.b_members) P.wchart[pc] = 1;
     upload(P.d_wchart, P.wchart, s);
     PGCP_CUDA(cudaStreamSynchronize(s));
+    // dropped meshes: their pieces keep the local maps (finite), so the final
+    // solve runs through; their output is set to NaN after the gather
+    P.mesh_status.assign(nmesh, PGCP_OK);
+    int nfailed = 0;
+    for (int mi = 0; mi < nmesh; ++mi) {
+        if (!mfail[mi]) continue;
+        ++nfailed;
+        P.mesh_status[mi] = PGCP_E_NUMERIC;
+        const MeshInfo& M = P.meshes[mi];
+        const int64_t r0 = P.voff[M.piece0], r1 = P.voff[M.piece0 + M.npiece];
+        PGCP_CUDA(cudaMemcpyAsync(P.welded.p + r0, P.local.p + r0, (r1 - r0) * sizeof(double2),
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+    if (nfailed) {   // the gather skips the pieces of dropped meshes (flag 2)
+        for (int mi = 0; mi < nmesh; ++mi)
+            if (mfail[mi])
+                for (int32_t pc = P.meshes[mi].piece0; pc < P.meshes[mi].piece0 + P.meshes[mi].npiece; ++pc)
+                    P.wchart[pc] = 2;
+        upload(P.d_wchart, P.wchart, s);
+    }
+    PGCP_CUDA(cudaStreamSynchronize(s));
+    if (nfailed == nmesh) fail(PGCP_E_NUMERIC, "every mesh of the batch left the welding domain");
     P.have_weld = 1;
 }
 
