@@ -58,7 +58,8 @@ def main(argv=None):
         part.global_solve()
         torch.cuda.synchronize()
         print(json.dumps({"case": "final", "nv": m.nv, **{k: part.stats[k] for k in
-                                                          ("dncp_iters", "final_iters", "pcg_ms")}}))
+                                                          ("dncp_iters", "dncp_refine", "dncp_relres", "final_iters",
+                                                           "pcg_ms", "ms_local", "ms_final")}}))
     return 0
 
 
