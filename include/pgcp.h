@@ -314,6 +314,43 @@ pgcp_status pgcp_gnn_train_step(pgcp_ctx* ctx, pgcp_gnn* gnn, const pgcp_part* p
 pgcp_status pgcp_gnn_predict(pgcp_ctx* ctx, const pgcp_gnn* gnn, const pgcp_part* part, double* x0);
 
 /*
+ * One-call forms of Algorithm 3 per variant (Section 4.4): partition, local
+ * DNCP maps, welds (+ disk or closed weld), final harmonic solve, gather.
+ * V [nv*3], F [nf*3], cut [n_cut*2] (or NULL with face_labels [nf]) and the
+ * output are DEVICE pointers; the output is uv [nv*2] (free, disk) or xyz
+ * [nv*3] (sphere).  The variant in the context options is ignored (each call
+ * sets its own); every other option applies.  st may be NULL.
+ */
+pgcp_status pgcp_free_boundary(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                               const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* uv_out,
+                               pgcp_stats* st);
+pgcp_status pgcp_disk(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                      const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* uv_out,
+                      pgcp_stats* st);
+pgcp_status pgcp_sphere(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                        const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* xyz_out,
+                        pgcp_stats* st);
+
+/*
+ * Batched one-call form: many independent meshes (open surfaces for free and
+ * disk, closed for sphere, per the context's variant) in one part, so every
+ * solve stage runs once for the whole batch (one persistent PCG launch over
+ * all pieces of all meshes).  Device pointers; outs[b] receives mesh b's map
+ * ([nv_b*2] or [nv_b*3]).  mesh_status (host int32 [n_mesh], may be NULL)
+ * gets each mesh's status (see pgcp_part_mesh_status): a mesh dropped by the
+ * welding is NaN and the call still returns PGCP_OK.
+ */
+typedef struct {
+    const double* V;
+    int64_t nv;
+    const int32_t* F;
+    int64_t nf;
+    const int32_t* face_labels;   /* [nf] piece label of every face */
+} pgcp_mesh_desc;
+pgcp_status pgcp_batch_run(pgcp_ctx* ctx, int32_t n_mesh, const pgcp_mesh_desc* meshes, double* const* outs,
+                           int32_t* mesh_status, pgcp_stats* st);
+
+/*
  * Self-test access to the device primitives the partition and the metrics
  * build on (no counterpart in the paper).  Device pointers, ordered on the
  * context stream.

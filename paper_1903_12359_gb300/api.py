@@ -95,6 +95,10 @@ SIGNATURES = {
     "pgcp_selftest_scan": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgcp_selftest_gemm_bf16": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]),
     "pgcp_autotune": (C.c_int, [_P, _P, C.c_int32, C.POINTER(Options), C.POINTER(C.c_double)]),
+    "pgcp_free_boundary": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, _P, C.POINTER(Stats)]),
+    "pgcp_disk": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, _P, C.POINTER(Stats)]),
+    "pgcp_sphere": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, _P, C.POINTER(Stats)]),
+    "pgcp_batch_run": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.POINTER(Stats)]),
     "pgcp_part_mesh_status": (C.c_int, [_P, _P]),
     "pgcp_gnn_num_params": (C.c_int64, []),
     "pgcp_gnn_create": (C.c_int, [_P, _P, C.POINTER(C.c_void_p)]),
@@ -273,6 +277,39 @@ class Context:
         self.check(load().pgcp_run(self.h, _ptr(Vd), Vd.shape[0], _ptr(Fd), Fd.shape[0], _ptr(cd),
                                    0 if cd is None else cd.shape[0], _ptr(ld), 0, _ptr(out), C.byref(st)))
         return out, st.as_dict()
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("nv", C.c_int64), ("F", C.c_void_p), ("nf", C.c_int64),
+                ("face_labels", C.c_void_p)]
+
+
+def one_call(ctx: "Context", variant: str, V, F, cut_edges=None, face_labels=None):
+    """pgcp_free_boundary / pgcp_disk / pgcp_sphere on device copies of the inputs;
+    returns (map tensor, stats dict)."""
+    fn = {"free": "pgcp_free_boundary", "disk": "pgcp_disk", "sphere": "pgcp_sphere"}[variant]
+    Vd, Fd = _dev(V, torch.float64), _dev(F, torch.int32)
+    cd = None if cut_edges is None else _dev(cut_edges, torch.int32)
+    ld = None if face_labels is None else _dev(face_labels, torch.int32)
+    out = torch.empty((Vd.shape[0], 3 if variant == "sphere" else 2), dtype=torch.float64, device="cuda")
+    st = Stats()
+    ctx.check(getattr(load(), fn)(ctx.h, _ptr(Vd), Vd.shape[0], _ptr(Fd), Fd.shape[0], _ptr(cd),
+                                  0 if cd is None else cd.shape[0], _ptr(ld), _ptr(out), C.byref(st)))
+    return out, st.as_dict()
+
+
+def batch_run(ctx: "Context", meshes):
+    """pgcp_batch_run on [(V, F, face_labels)]: (list of map tensors, list of status names, stats)."""
+    keep = [(_dev(m[0], torch.float64), _dev(m[1], torch.int32), _dev(m[2], torch.int32)) for m in meshes]
+    dim = 3 if ctx.options.variant == SPHERE else 2
+    outs = [torch.empty((v.shape[0], dim), dtype=torch.float64, device="cuda") for v, _, _ in keep]
+    descs = (MeshDesc * len(keep))(*[MeshDesc(v.data_ptr(), v.shape[0], f.data_ptr(), f.shape[0], l.data_ptr())
+                                     for v, f, l in keep])
+    ptrs = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    status = (C.c_int32 * len(keep))()
+    st = Stats()
+    ctx.check(load().pgcp_batch_run(ctx.h, len(keep), descs, ptrs, status, C.byref(st)))
+    return outs, [STATUS.get(v, str(v)) for v in status], st.as_dict()
 
 
 class Part:

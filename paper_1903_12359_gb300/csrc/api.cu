@@ -420,6 +420,83 @@ pgcp_status pgcp_run(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* 
     return s;
 }
 
+namespace {
+pgcp_status run_variant(pgcp_ctx* ctx, int32_t variant, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                        const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* out,
+                        pgcp_stats* st) {
+    if (!ctx) return PGCP_E_ARG;
+    const int32_t saved = ctx->opt.variant;
+    ctx->opt.variant = variant;
+    const pgcp_status s = pgcp_run(ctx, V, nv, F, nf, cut, n_cut, face_labels, 0, out, st);
+    ctx->opt.variant = saved;
+    return s;
+}
+}  // namespace
+
+pgcp_status pgcp_free_boundary(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                               const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* uv_out,
+                               pgcp_stats* st) {
+    return run_variant(ctx, PGCP_FREE, V, nv, F, nf, cut, n_cut, face_labels, uv_out, st);
+}
+
+pgcp_status pgcp_disk(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                      const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* uv_out,
+                      pgcp_stats* st) {
+    return run_variant(ctx, PGCP_DISK, V, nv, F, nf, cut, n_cut, face_labels, uv_out, st);
+}
+
+pgcp_status pgcp_sphere(pgcp_ctx* ctx, const double* V, int64_t nv, const int32_t* F, int64_t nf,
+                        const int32_t* cut, int64_t n_cut, const int32_t* face_labels, double* xyz_out,
+                        pgcp_stats* st) {
+    return run_variant(ctx, PGCP_SPHERE, V, nv, F, nf, cut, n_cut, face_labels, xyz_out, st);
+}
+
+pgcp_status pgcp_batch_run(pgcp_ctx* ctx, int32_t n_mesh, const pgcp_mesh_desc* meshes, double* const* outs,
+                           int32_t* mesh_status, pgcp_stats* st) {
+    pgcp_part* part = nullptr;
+    pgcp_status s = guard(ctx, [&] {
+        if (!ctx || n_mesh <= 0 || !meshes || !outs) fail(PGCP_E_ARG, "bad batch arguments");
+        for (int32_t b = 0; b < n_mesh; ++b)
+            if (!outs[b] || !meshes[b].face_labels) fail(PGCP_E_ARG, "batch mesh without labels or output");
+    });
+    if (s != PGCP_OK) return s;
+    std::vector<const double*> V(n_mesh);
+    std::vector<const int32_t*> F(n_mesh), Lb(n_mesh);
+    std::vector<int64_t> nv(n_mesh), nf(n_mesh);
+    for (int32_t b = 0; b < n_mesh; ++b) {
+        V[b] = meshes[b].V;
+        F[b] = meshes[b].F;
+        Lb[b] = meshes[b].face_labels;
+        nv[b] = meshes[b].nv;
+        nf[b] = meshes[b].nf;
+    }
+    s = pgcp_partition_batch(ctx, n_mesh, V.data(), nv.data(), F.data(), nf.data(), Lb.data(), 0,
+                             ctx->opt.variant == PGCP_SPHERE, &part);
+    if (s == PGCP_OK) s = pgcp_local_param(ctx, part);
+    if (s == PGCP_OK) s = pgcp_weld(ctx, part);
+    if (s == PGCP_OK) {
+        const int dim = ctx->opt.variant == PGCP_SPHERE ? 3 : 2;
+        int64_t total = 0;
+        for (int32_t b = 0; b < n_mesh; ++b) total += nv[b];
+        s = guard(ctx, [&] {
+            DBuf<double> all;
+            all.alloc(dim * total, ctx->stream);
+            const pgcp_status g = pgcp_global_solve(ctx, part, all.p, 0, st);
+            if (g != PGCP_OK) throw Thrown(g, ctx->last_error);
+            int64_t off = 0;
+            for (int32_t b = 0; b < n_mesh; ++b) {
+                PGCP_CUDA(cudaMemcpyAsync(outs[b], all.p + dim * off, dim * nv[b] * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+                off += nv[b];
+            }
+            PGCP_CUDA(cudaStreamSynchronize(ctx->stream));
+        });
+    }
+    if (part && mesh_status) pgcp_part_mesh_status(part, mesh_status);
+    if (part) pgcp_part_free(part);
+    return s;
+}
+
 pgcp_status pgcp_selftest_sort(pgcp_ctx* ctx, uint64_t* keys, int32_t* vals, int64_t n, int32_t bits) {
     return guard(ctx, [&] {
         if (!keys || !vals || n < 0 || bits < 0 || bits > 64) fail(PGCP_E_ARG, "bad sort arguments");
