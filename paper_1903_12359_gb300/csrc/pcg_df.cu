@@ -718,6 +718,279 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_dyn(RunArgs<A> a) {
     }
 }
 
+// Round-robin static schedule.  Block b takes the chunks b, b + G, b + 2G, ...
+// (G blocks), so every block samples the whole matrix; nothing is fetched
+// from a counter and no barrier separates chunks.  Partial sums go through
+// warp shuffles into a per-piece table in shared memory; at the end of a phase
+// the block adds each piece's total and chunk count to the global
+// accumulators, and the block that completes a piece computes its scalars
+// (as in the dynamic schedule).  Up to RR_MAXSEG pieces.
+constexpr int RR_MAXSEG = 256;
+
+template <typename A, int MINB>
+__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_rr(RunArgs<A> a) {
+    using S = typename A::S;
+    using V = typename A::V;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double tab[RR_MAXSEG][4];
+    __shared__ int tcnt[RR_MAXSEG];
+    __shared__ double ssc[RR_MAXSEG][2];     // this phase's beta (B) or alpha (A) per piece
+    __shared__ unsigned char sdn[RR_MAXSEG][2];
+    const int nseg = a.nseg;
+    const int lane = threadIdx.x & 31;
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ colp = a.col;
+    const S* __restrict__ valp = a.val;
+    const float* __restrict__ dgp = a.dgn;
+    const int G = gridDim.x;
+    unsigned long long wrows = 0, wnnz = 0;
+    // warp sum of a double-float value, added into the piece's table entry
+    auto warp_add = [&](float2 v, double* dst) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+            t.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+            v = df_add(v, t);
+        }
+        if (lane == 0) atomicAdd(dst, df_to_d(v));
+    };
+    int k = 0;
+    for (; k < a.max_iters; ++k) {
+        const double* RRk = a.RR + (k % 3) * 2 * nseg;
+        double* RRn = a.RR + ((k + 1) % 3) * 2 * nseg;
+        double* RDn = a.RD + ((k + 1) % 3) * 2 * nseg;
+        double* PQk = a.PQ + (k % 2) * 2 * nseg;
+        const double* BETk = a.BETA + (k % 2) * 2 * nseg;
+        double* BETn = a.BETA + ((k + 1) % 2) * 2 * nseg;
+        double* ALPk = a.ALPHA + (k % 2) * 2 * nseg;
+        unsigned* CB = a.CNTB + (k % 2) * nseg;
+        unsigned* CA = a.CNTA + (k % 2) * nseg;
+        // ---------------- phase B: p = r + beta p, q = A~ r + beta q, <p, q>
+        if (blockIdx.x == 0) {
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) {
+                RRn[i] = 0.0;
+                RDn[i] = 0.0;
+            }
+            for (int i = threadIdx.x; i < nseg; i += blockDim.x) a.CNTB[((k + 1) % 2) * nseg + i] = 0u;
+        }
+        for (int i = threadIdx.x; i < nseg; i += blockDim.x) {
+            tab[i][0] = tab[i][1] = 0.0;
+            tcnt[i] = 0;
+            ssc[i][0] = __ldcg(BETk + 2 * i);
+            ssc[i][1] = __ldcg(BETk + 2 * i + 1);
+            sdn[i][0] = __ldcg(a.DONEF + 2 * i) != 0u;
+            sdn[i][1] = __ldcg(a.DONEF + 2 * i + 1) != 0u;
+        }
+        __syncthreads();
+        bool any = false;
+        {
+            int c = blockIdx.x;
+            int bn = 0, en = 0;
+            DfRun chn = c < a.nchunks ? a.chunks[c] : DfRun{};
+            if (c < a.nchunks && chn.lo + (int)threadIdx.x < chn.hi) {
+                bn = __ldg(rp + chn.lo + threadIdx.x);
+                en = __ldg(rp + chn.lo + threadIdx.x + 1);
+            }
+            for (; c < a.nchunks; c += G) {
+                const DfRun ch = chn;
+                const int b = bn, e = en;
+                // next chunk of this block: its descriptor and row bounds now, its streams into L2
+                const int cn = c + G;
+                int nrow = -1;
+                bn = en = 0;
+                if (cn < a.nchunks) {
+                    chn = a.chunks[cn];
+                    if (chn.lo + (int)threadIdx.x < chn.hi) {
+                        nrow = chn.lo + threadIdx.x;
+                        bn = __ldg(rp + nrow);
+                        en = __ldg(rp + nrow + 1);
+                        prefetch_l2(a.p + nrow);
+                        prefetch_l2(a.q + nrow);
+                        prefetch_l2(a.r + nrow);
+                    }
+                }
+                const int seg = ch.seg;
+                const bool d0 = sdn[seg][0], d1 = sdn[seg][1];
+                if (d0 && d1) continue;
+                any = true;
+                const S beta0 = A::from_d(ssc[seg][0]), beta1 = A::from_d(ssc[seg][1]);
+                S acc0 = A::zero(), acc1 = A::zero();
+                const int row = ch.lo + threadIdx.x;
+                if (row < ch.hi && b < e) {
+                    S w0 = A::zero(), w1 = A::zero();
+                    int j = b;
+                    for (; j + 4 <= e; j += 4) {
+                        int32_t cc[4];
+                        S v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            cc[u] = __ldg(colp + j + u);
+                            v[u] = __ldg(valp + j + u);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) spmv_entry<A>(cc[u], v[u], a.r, w0, w1);
+                    }
+                    for (; j < e; ++j) spmv_entry<A>(__ldg(colp + j), __ldg(valp + j), a.r, w0, w1);
+                    const V rr = a.r[row];
+                    const V pp = a.p[row], qq = a.q[row];
+                    S px = A::cx(pp), py = A::cy(pp), qx = A::cx(qq), qy = A::cy(qq);
+                    if (!d0) {
+                        px = A::fma(A::cx(rr), beta0, px);
+                        qx = A::fma(w0, beta0, qx);
+                        acc0 = A::fma(acc0, px, qx);
+                    }
+                    if (!d1) {
+                        py = A::fma(A::cy(rr), beta1, py);
+                        qy = A::fma(w1, beta1, qy);
+                        acc1 = A::fma(acc1, py, qy);
+                    }
+                    a.p[row] = A::pack(px, py);
+                    a.q[row] = A::pack(qx, qy);
+                }
+                if (nrow >= 0 && en > bn) {
+                    prefetch_l2(colp + bn);
+                    prefetch_l2(valp + bn);
+                    prefetch_l2(valp + en - 1);
+                }
+                warp_add(A::as_df(acc0), &tab[seg][0]);
+                warp_add(A::as_df(acc1), &tab[seg][1]);
+                if (threadIdx.x == 0) {
+                    tcnt[seg] += 1;
+                    wrows += (unsigned long long)ch.frows;
+                    wnnz += (unsigned long long)ch.fnnz;
+                }
+            }
+        }
+        __syncthreads();
+        for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+            const int m = tcnt[sg];
+            if (m == 0) continue;
+            atomicAdd(&PQk[2 * sg], tab[sg][0]);
+            atomicAdd(&PQk[2 * sg + 1], tab[sg][1]);
+            __threadfence();
+            const unsigned old = atomicAdd(&CB[sg], (unsigned)m);
+            if (old + (unsigned)m == (unsigned)a.nch[sg]) {   // this block completed <p, q>
+                __threadfence();
+                const double pq0 = __ldcg(PQk + 2 * sg), pq1 = __ldcg(PQk + 2 * sg + 1);
+                const double rr0 = __ldcg(RRk + 2 * sg), rr1 = __ldcg(RRk + 2 * sg + 1);
+                double al0, al1;
+                if (a.dncp) {
+                    const double den = pq0 + pq1;
+                    al0 = al1 = den > 0.0 ? (rr0 + rr1) / den : 0.0;
+                } else {
+                    al0 = (!__ldcg(a.DONEF + 2 * sg) && pq0 > 0.0) ? rr0 / pq0 : 0.0;
+                    al1 = (!__ldcg(a.DONEF + 2 * sg + 1) && pq1 > 0.0) ? rr1 / pq1 : 0.0;
+                }
+                __stcg(ALPk + 2 * sg, al0);
+                __stcg(ALPk + 2 * sg + 1, al1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && any) *(volatile unsigned*)&a.ACT[k % 3] = 1u;
+        grid.sync();
+        // ---------------- phase A: x~ += alpha p, r -= alpha q, norms
+        if (blockIdx.x == 0) {
+            double* z = a.PQ + ((k + 1) % 2) * 2 * nseg;
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) z[i] = 0.0;
+            for (int i = threadIdx.x; i < nseg; i += blockDim.x) a.CNTA[((k + 1) % 2) * nseg + i] = 0u;
+            if (threadIdx.x == 0) a.ACT[(k + 1) % 3] = 0;
+        }
+        for (int i = threadIdx.x; i < nseg; i += blockDim.x) {
+            tab[i][0] = tab[i][1] = tab[i][2] = tab[i][3] = 0.0;
+            tcnt[i] = 0;
+            ssc[i][0] = __ldcg(ALPk + 2 * i);
+            ssc[i][1] = __ldcg(ALPk + 2 * i + 1);
+            sdn[i][0] = __ldcg(a.DONEF + 2 * i) != 0u;
+            sdn[i][1] = __ldcg(a.DONEF + 2 * i + 1) != 0u;
+        }
+        __syncthreads();
+        DfRun chn = blockIdx.x < (unsigned)a.nchunks ? a.chunks[blockIdx.x] : DfRun{};
+        for (int c = blockIdx.x; c < a.nchunks; c += G) {
+            const DfRun ch = chn;
+            const int cn = c + G;
+            if (cn < a.nchunks) {
+                chn = a.chunks[cn];
+                const int nrow = chn.lo + threadIdx.x;
+                if (nrow < chn.hi) {
+                    prefetch_l2(a.x + nrow);
+                    prefetch_l2(a.r + nrow);
+                    prefetch_l2(a.p + nrow);
+                    prefetch_l2(a.q + nrow);
+                }
+            }
+            const int seg = ch.seg;
+            const bool d0 = sdn[seg][0], d1 = sdn[seg][1];
+            if (d0 && d1) continue;
+            const S al0 = A::from_d(ssc[seg][0]), al1 = A::from_d(ssc[seg][1]);
+            S rr0 = A::zero(), rr1 = A::zero();
+            float rd0 = 0.f, rd1 = 0.f;
+            const int row = ch.lo + threadIdx.x;
+            if (row < ch.hi) {
+                const float d = __ldg(dgp + row);
+                if (d != 0.f) {
+                    const V xx = a.x[row], rv = a.r[row];
+                    const V pp = a.p[row], qq = a.q[row];
+                    const S x0 = A::fma(A::cx(xx), al0, A::cx(pp)), x1 = A::fma(A::cy(xx), al1, A::cy(pp));
+                    const S r0 = A::fma(A::cx(rv), A::neg(al0), A::cx(qq));
+                    const S r1 = A::fma(A::cy(rv), A::neg(al1), A::cy(qq));
+                    a.x[row] = A::pack(x0, x1);
+                    a.r[row] = A::pack(r0, r1);
+                    rr0 = A::fma(rr0, r0, r0);
+                    rr1 = A::fma(rr1, r1, r1);
+                    const float l0 = A::lead(r0), l1 = A::lead(r1);
+                    rd0 = fmaf(d * l0, l0, rd0);
+                    rd1 = fmaf(d * l1, l1, rd1);
+                }
+            }
+            warp_add(A::as_df(rr0), &tab[seg][0]);
+            warp_add(A::as_df(rr1), &tab[seg][1]);
+            warp_add(make_float2(rd0, 0.f), &tab[seg][2]);
+            warp_add(make_float2(rd1, 0.f), &tab[seg][3]);
+            if (threadIdx.x == 0) tcnt[seg] += 1;
+        }
+        __syncthreads();
+        for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+            const int m = tcnt[sg];
+            if (m == 0) continue;
+            atomicAdd(&RRn[2 * sg], tab[sg][0]);
+            atomicAdd(&RRn[2 * sg + 1], tab[sg][1]);
+            atomicAdd(&RDn[2 * sg], tab[sg][2]);
+            atomicAdd(&RDn[2 * sg + 1], tab[sg][3]);
+            __threadfence();
+            const unsigned old = atomicAdd(&CA[sg], (unsigned)m);
+            if (old + (unsigned)m == (unsigned)a.nch[sg]) {   // this block completed the norms
+                __threadfence();
+                const double n0 = __ldcg(RRn + 2 * sg), n1 = __ldcg(RRn + 2 * sg + 1);
+                const double o0 = __ldcg(RRk + 2 * sg), o1 = __ldcg(RRk + 2 * sg + 1);
+                const double e0 = __ldcg(RDn + 2 * sg), e1 = __ldcg(RDn + 2 * sg + 1);
+                const double t0 = a.THR[2 * sg], t1 = a.THR[2 * sg + 1];
+                if (a.dncp) {
+                    const double bt = (o0 + o1) > 0.0 ? (n0 + n1) / (o0 + o1) : 0.0;
+                    __stcg(BETn + 2 * sg, bt);
+                    __stcg(BETn + 2 * sg + 1, bt);
+                    if (e0 + e1 <= t0 + t1) {
+                        __stcg(a.DONEF + 2 * sg, 1u);
+                        __stcg(a.DONEF + 2 * sg + 1, 1u);
+                    }
+                } else {
+                    __stcg(BETn + 2 * sg, o0 > 0.0 ? n0 / o0 : 0.0);
+                    __stcg(BETn + 2 * sg + 1, o1 > 0.0 ? n1 / o1 : 0.0);
+                    if (e0 <= t0) __stcg(a.DONEF + 2 * sg, 1u);
+                    if (e1 <= t1) __stcg(a.DONEF + 2 * sg + 1, 1u);
+                }
+            }
+        }
+        grid.sync();
+        if (*(volatile unsigned*)&a.ACT[k % 3] == 0u) break;
+    }
+    if (threadIdx.x == 0) {
+        if (wrows) atomicAdd(&a.work[0], wrows);
+        if (wnnz) atomicAdd(&a.work[1], wnnz);
+        if (blockIdx.x == 0) a.out_iters[0] = k;
+    }
+}
+
 // Initial state of the dynamic schedule: converged flags from <r0, r0>, beta 0.
 __global__ void k_dyn_init(int nseg, int dncp, const double* __restrict__ RD0, const double* __restrict__ THR,
                            unsigned int* __restrict__ DONEF, double* __restrict__ BETA0) {
@@ -912,6 +1185,11 @@ void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSyste
     PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dyn, kd, RUN_THREADS, 0));
     if (per_sm_dyn <= 0) fail(PGCP_E_CUDA, "dynamically scheduled PCG kernel cannot be resident");
     D.dyn_grid = per_sm_dyn * ctx->num_sms;
+    int per_sm_rr = 0;
+    const void* kr = D.minb == 3 ? (const void*)k_pcg_rr<A, 3> : (const void*)k_pcg_rr<A, 4>;
+    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rr, kr, RUN_THREADS, 0));
+    if (per_sm_rr <= 0) fail(PGCP_E_CUDA, "round-robin PCG kernel cannot be resident");
+    D.rr_grid = per_sm_rr * ctx->num_sms;
     const size_t vb = sizeof(typename A::V);
     D.x.alloc(n * vb, s);
     D.r.alloc(n * vb, s);
@@ -930,7 +1208,7 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, D.RR.p,
                                                             D.RD.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
-    if (D.dyn) {
+    if (D.sched >= 2) {
         { k_dyn_init<<<(unsigned)std::max<int64_t>(1, ceil_div((int64_t)P.K, 256)), 256, 0, s>>>(
             P.K, D.dncp, D.RD.p, D.THR.p, D.DONEF.p, D.BETA.p); ::pgcp::note_launch(); }
         D.CTR.zero();
@@ -952,9 +1230,13 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     a.BETA = D.BETA.p;
     a.DONEF = D.DONEF.p;
     void* args[] = {(void*)&a};
-    if (D.dyn) {
+    if (D.sched == 2) {
         const void* kern = D.minb == 3 ? (const void*)k_pcg_dyn<A, 3> : (const void*)k_pcg_dyn<A, 4>;
         const int grid = std::max(1, std::min(D.dyn_grid, D.nchunks));
+        { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    } else if (D.sched == 3) {
+        const void* kern = D.minb == 3 ? (const void*)k_pcg_rr<A, 3> : (const void*)k_pcg_rr<A, 4>;
+        const int grid = std::max(1, std::min(D.rr_grid, D.nchunks));
         { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
     } else {
         const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
@@ -984,8 +1266,9 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     if (bps != 0 && bps != 3 && bps != 4) fail(PGCP_E_ARG, "pcg_blocks_per_sm must be 0, 3 or 4");
     D.minb = bps == 3 ? 3 : 4;
     const int sched = ctx->opt.pcg_schedule;
-    if (sched < 0 || sched > 2) fail(PGCP_E_ARG, "pcg_schedule must be 0, 1 or 2");
-    D.dyn = sched == 2;
+    if (sched < 0 || sched > 3) fail(PGCP_E_ARG, "pcg_schedule must be 0, 1, 2 or 3");
+    D.sched = sched == 0 ? 1 : sched;
+    if (D.sched == 3 && P.K > RR_MAXSEG) D.sched = 1;   // the round-robin tables hold RR_MAXSEG pieces
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;
     cnt.alloc(n, s);

@@ -238,7 +238,7 @@ struct DfSystem {
     DBuf<int32_t> out_it;
     DBuf<unsigned long long> work;
     // dynamic schedule: chunks inside pieces, per-piece chunk counts, counters
-    int dyn = 1, dyn_grid = 0;
+    int sched = 1, dyn_grid = 0, rr_grid = 0;   // 1 static runs, 2 dynamic chunks, 3 round-robin chunks
     int32_t nchunks = 0;
     DBuf<DfRun> chunks;
     DBuf<int32_t> nch;

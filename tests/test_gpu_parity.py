@@ -229,3 +229,23 @@ def test_partition_full_size_bit_exact(api):
     assert np.array_equal(fl, P.face_label)
     assert np.array_equal(verts, np.concatenate(P.verts))
     assert np.array_equal(loops, np.concatenate(P.loops))
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3], ids=["static", "dynamic", "roundrobin"])
+@pytest.mark.parametrize("name", ["grid4x2", "sphere"])
+def test_dncp_and_final_under_every_pcg_schedule(api, name, schedule):
+    """The three work schedules of the mixed-precision PCG give the oracle's map."""
+    m, variant = _case(name)
+    ctx, part = _gpu_part(api, m, variant, precision=1, tol=1e-13, local_precision=2, pcg_schedule=schedule)
+    part.local_param()
+    u = part.coords(0).cpu().numpy()
+    P = o_partition(m.V, m.F, face_labels=m.face_labels)
+    voff = np.concatenate([[0], np.cumsum([v.size for v in P.verts])])
+    for i in range(P.K):
+        ll = np.searchsorted(P.verts[i], P.loops[i])
+        ref, _ = o_dncp(m.V[P.verts[i]], P.local_F[i], ll)
+        assert np.abs(u[voff[i]:voff[i + 1]] - ref).max() < 1e-9
+    part.weld()
+    out = part.global_solve().cpu().numpy()
+    ref = o_pgcp(m.V, m.F, face_labels=m.face_labels, variant=variant).out
+    assert np.abs(out - ref).max() < 1e-8
