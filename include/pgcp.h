@@ -70,7 +70,9 @@ typedef struct {
     int32_t pcg_schedule;     /* mixed-precision PCG work schedule: 1 static (each block a fixed row
                                  range), 2 dynamic (blocks take 256-row chunks from a counter),
                                  3 round-robin (block b takes chunks b, b + G, ...; up to 256
-                                 pieces, else 1); autotuner output, 0 = default static */
+                                 pieces, else 1), 4 static with one reduction per iteration
+                                 (Chronopoulos-Gear form; up to 16 pieces per block, else 1);
+                                 autotuner output, 0 = default static */
     int32_t reserved[3];
 } pgcp_options;
 
@@ -265,7 +267,7 @@ pgcp_status pgcp_part_mesh_status(const pgcp_part* part, int32_t* status);
  * probe_iters (>= 10) capped DNCP iterations of `part` for each candidate and
  * stores the fastest in the context options (and in *chosen):
  *   mixed-precision local solves: pcg_blocks_per_sm in {3, 4} x pcg_schedule
- *   in {static, dynamic};  FP64 local solves: spmv_lanes in {1, 2, 4} x
+ *   in {static, dynamic, round-robin, one reduction};  FP64 local solves: spmv_lanes in {1, 2, 4} x
  *   block_rows_log2 in {8, 9, 10}.
  * The probes overwrite the part's local map: call pgcp_local_param afterwards.
  * ms_per_iter (may be NULL): the winner's kernel time per iteration.

@@ -151,6 +151,13 @@ struct RunArgs {
     int32_t max_iters;
     int32_t dncp;
     unsigned long long* work;           // [2] free rows, stored entries, summed over iterations
+    // single-reduction schedule (k_pcg_cg1): second residual slot, A r in two
+    // slots, s = A p in two slots (slot 0 is q), <r, A r> accumulators [3][2 nseg]
+    typename A::V* r1;
+    typename A::V* w0;
+    typename A::V* w1;
+    typename A::V* s1;
+    double* DL;
     // dynamic schedule (k_pcg_dyn)
     const DfRun* __restrict__ chunks;   // RUN_THREADS-row chunks inside pieces
     int32_t nchunks;
@@ -991,6 +998,207 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_rr(RunArgs<A> a) {
     }
 }
 
+// Single-reduction schedule: CG in the form of Chronopoulos and Gear
+// ("s-step iterative methods for symmetric linear systems", 1989): with
+// w = A~ r and s = A~ p kept as vectors, one iteration needs one SpMV and one
+// combined reduction of gamma = <r, r>, delta = <r, w>:
+//   beta_k = gamma_k / gamma_{k-1},  alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_{k-1})
+//   p_k = r_k + beta_k p_{k-1};  s_k = w_k + beta_k s_{k-1}
+//   x_{k+1} = x_k + alpha_k p_k;  r_{k+1} = r_k - alpha_k s_k;  w_{k+1} = A~ r_{k+1}
+// so one grid sync per iteration.  A row's SpMV needs its neighbours' r_{k+1},
+// which is formed on the fly from their r_k, w_k and s_{k-1}; r, w and s are
+// double-buffered so no block overwrites what another still gathers.
+constexpr int CG1_MAXRUNS = 16;
+
+template <typename A>
+__device__ __forceinline__ typename A::V next_r(const typename A::V& r, const typename A::V& w, const typename A::V& sp,
+                                                typename A::S al0, typename A::S al1, typename A::S be0,
+                                                typename A::S be1) {
+    const typename A::S s0 = A::fma(A::cx(w), be0, A::cx(sp)), s1 = A::fma(A::cy(w), be1, A::cy(sp));
+    return A::pack(A::fma(A::cx(r), A::neg(al0), s0), A::fma(A::cy(r), A::neg(al1), s1));
+}
+
+template <typename A, int MINB>
+__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_cg1(RunArgs<A> a) {
+    using S = typename A::S;
+    using V = typename A::V;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float2 red[6 * (RUN_THREADS / 32)];
+    __shared__ double sc[2][4];
+    __shared__ int sflag[2][2];
+    __shared__ double alpha_prev[CG1_MAXRUNS][2];
+    const int nseg = a.nseg;
+    const int rb = a.run_off[blockIdx.x], re = a.run_off[blockIdx.x + 1];
+    const int32_t* __restrict__ rp = a.rp;
+    const int32_t* __restrict__ colp = a.col;
+    const S* __restrict__ valp = a.val;
+    const float* __restrict__ dgp = a.dgn;
+    V* const rbuf[2] = {a.r, a.r1};
+    V* const wbuf[2] = {a.w0, a.w1};
+    V* const sbuf[2] = {a.q, a.s1};
+    unsigned long long wrows = 0, wnnz = 0;
+    // ---------------- set-up: w_0 = A~ r_0, delta_0 = <r_0, w_0>
+    for (int ri = rb; ri < re; ++ri) {
+        const DfRun run = a.runs[ri];
+        S d0 = A::zero(), d1 = A::zero();
+        for (int row = run.lo + threadIdx.x; row < run.hi; row += blockDim.x) {
+            const int b = __ldg(rp + row), e = __ldg(rp + row + 1);
+            S w0 = A::zero(), w1 = A::zero();
+            for (int j = b; j < e; ++j) spmv_entry<A>(__ldg(colp + j), __ldg(valp + j), a.r, w0, w1);
+            const V r = a.r[row];
+            a.w0[row] = A::pack(w0, w1);
+            a.s1[row] = A::vzero();
+            d0 = A::fma(d0, A::cx(r), w0);
+            d1 = A::fma(d1, A::cy(r), w1);
+        }
+        float2 pv[2] = {A::as_df(d0), A::as_df(d1)};
+        double v[2];
+        block_sum_df<2>(pv, red, v);
+        if (threadIdx.x == 0) {
+            atomicAdd(&a.DL[2 * run.seg], v[0]);
+            atomicAdd(&a.DL[2 * run.seg + 1], v[1]);
+        }
+        if (threadIdx.x < 2 && ri - rb < CG1_MAXRUNS) alpha_prev[ri - rb][threadIdx.x] = INFINITY;
+    }
+    grid.sync();
+    int k = 0;
+    for (; k < a.max_iters; ++k) {
+        // four accumulator slots: k (read), k - 1 (read), k + 1 (filled now), k + 2 (cleared now)
+        const double* Gk = a.RR + (k % 4) * 2 * nseg;
+        const double* Gm = a.RR + ((k + 3) % 4) * 2 * nseg;
+        const double* Dk = a.DL + (k % 4) * 2 * nseg;
+        const double* RDk = a.RD + (k % 4) * 2 * nseg;
+        double* Gn = a.RR + ((k + 1) % 4) * 2 * nseg;
+        double* Dn = a.DL + ((k + 1) % 4) * 2 * nseg;
+        double* RDn = a.RD + ((k + 1) % 4) * 2 * nseg;
+        const V* __restrict__ rk = rbuf[k & 1];
+        const V* __restrict__ wk = wbuf[k & 1];
+        const V* __restrict__ sm = sbuf[(k + 1) & 1];   // s_{k-1}
+        V* rn = rbuf[(k + 1) & 1];
+        V* wn = wbuf[(k + 1) & 1];
+        V* sk = sbuf[k & 1];
+        if (blockIdx.x == 0) {
+            double* g2 = a.RR + ((k + 2) % 4) * 2 * nseg;
+            double* d2 = a.DL + ((k + 2) % 4) * 2 * nseg;
+            double* e2 = a.RD + ((k + 2) % 4) * 2 * nseg;
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) {
+                g2[i] = 0.0;
+                d2[i] = 0.0;
+                e2[i] = 0.0;
+            }
+            if (threadIdx.x == 0) a.ACT[(k + 1) % 3] = 0;
+        }
+        bool any = false;
+        for (int ri = rb; ri < re; ++ri) {
+            const DfRun run = a.runs[ri];
+            const int s = run.seg, slot = ri & 1, lr = ri - rb;
+            if (threadIdx.x == 0) {
+                const bool d0 = piece_done(RDk, a.THR, s, 0, a.dncp);
+                const bool d1 = piece_done(RDk, a.THR, s, 1, a.dncp);
+                double be[2] = {0.0, 0.0}, al[2] = {0.0, 0.0};
+                const double g0 = __ldcg(Gk + 2 * s), g1 = __ldcg(Gk + 2 * s + 1);
+                const double e0 = __ldcg(Dk + 2 * s), e1 = __ldcg(Dk + 2 * s + 1);
+                if (a.dncp) {
+                    const double g = g0 + g1, dl = e0 + e1;
+                    const double gm = k > 0 ? __ldcg(Gm + 2 * s) + __ldcg(Gm + 2 * s + 1) : 0.0;
+                    const double b = (k > 0 && gm > 0.0) ? g / gm : 0.0;
+                    const double ap = alpha_prev[lr][0];
+                    const double den = dl - (ap > 0.0 && isfinite(ap) ? b * g / ap : 0.0);
+                    be[0] = be[1] = b;
+                    al[0] = al[1] = den > 0.0 ? g / den : 0.0;
+                } else {
+                    const double gg[2] = {g0, g1}, ee[2] = {e0, e1};
+                    for (int c = 0; c < 2; ++c) {
+                        const double gm = k > 0 ? __ldcg(Gm + 2 * s + c) : 0.0;
+                        const double b = (k > 0 && gm > 0.0) ? gg[c] / gm : 0.0;
+                        const double ap = alpha_prev[lr][c];
+                        const double den = ee[c] - (ap > 0.0 && isfinite(ap) ? b * gg[c] / ap : 0.0);
+                        be[c] = b;
+                        al[c] = den > 0.0 ? gg[c] / den : 0.0;
+                    }
+                    if (d0) al[0] = be[0] = 0.0;
+                    if (d1) al[1] = be[1] = 0.0;
+                }
+                sc[slot][0] = al[0];
+                sc[slot][1] = al[1];
+                sc[slot][2] = be[0];
+                sc[slot][3] = be[1];
+                sflag[slot][0] = d0;
+                sflag[slot][1] = d1;
+                if (!(d0 && d1)) {
+                    alpha_prev[lr][0] = al[0];
+                    alpha_prev[lr][1] = al[1];
+                }
+            }
+            __syncthreads();
+            const bool d0 = sflag[slot][0], d1 = sflag[slot][1];
+            if (d0 && d1) continue;
+            any = true;
+            const S al0 = A::from_d(sc[slot][0]), al1 = A::from_d(sc[slot][1]);
+            const S be0 = A::from_d(sc[slot][2]), be1 = A::from_d(sc[slot][3]);
+            S g0 = A::zero(), g1 = A::zero(), e0 = A::zero(), e1 = A::zero();
+            float rd0 = 0.f, rd1 = 0.f;
+            for (int row = run.lo + threadIdx.x; row < run.hi; row += blockDim.x) {
+                const float d = __ldg(dgp + row);
+                if (d == 0.f) continue;   // fixed row: r, w, s stay 0
+                const V r = rk[row], w = wk[row], spv = sm[row], pv = a.p[row], xv = a.x[row];
+                const S p0 = A::fma(A::cx(r), be0, A::cx(pv)), p1 = A::fma(A::cy(r), be1, A::cy(pv));
+                const S s0 = A::fma(A::cx(w), be0, A::cx(spv)), s1 = A::fma(A::cy(w), be1, A::cy(spv));
+                const S x0 = A::fma(A::cx(xv), al0, p0), x1 = A::fma(A::cy(xv), al1, p1);
+                const S r0 = A::fma(A::cx(r), A::neg(al0), s0), r1 = A::fma(A::cy(r), A::neg(al1), s1);
+                a.p[row] = A::pack(p0, p1);
+                sk[row] = A::pack(s0, s1);
+                a.x[row] = A::pack(x0, x1);
+                rn[row] = A::pack(r0, r1);
+                // w_{k+1} = A~ r_{k+1}: the neighbours' r_{k+1} formed from their r_k, w_k, s_{k-1}
+                S w0 = A::zero(), w1 = A::zero();
+                const int b = __ldg(rp + row), e = __ldg(rp + row + 1);
+                for (int j = b; j < e; ++j) {
+                    const int32_t c = __ldg(colp + j);
+                    const S v = __ldg(valp + j);
+                    const bool cross = c < 0;
+                    const int cc = cross ? ~c : c;
+                    const V rc = next_r<A>(rk[cc], wk[cc], sm[cc], al0, al1, be0, be1);
+                    const S a0 = cross ? A::cy(rc) : A::cx(rc);
+                    const S a1 = cross ? A::cx(rc) : A::cy(rc);
+                    w0 = A::fma(w0, cross ? A::neg(v) : v, a0);
+                    w1 = A::fma(w1, v, a1);
+                }
+                wn[row] = A::pack(w0, w1);
+                g0 = A::fma(g0, r0, r0);
+                g1 = A::fma(g1, r1, r1);
+                e0 = A::fma(e0, r0, w0);
+                e1 = A::fma(e1, r1, w1);
+                const float l0 = A::lead(r0), l1 = A::lead(r1);
+                rd0 = fmaf(d * l0, l0, rd0);
+                rd1 = fmaf(d * l1, l1, rd1);
+            }
+            float2 pv[6] = {A::as_df(g0), A::as_df(g1), A::as_df(e0), A::as_df(e1), make_float2(rd0, 0.f),
+                            make_float2(rd1, 0.f)};
+            double v[6];
+            block_sum_df<6>(pv, red, v);
+            if (threadIdx.x == 0) {
+                atomicAdd(&Gn[2 * s], v[0]);
+                atomicAdd(&Gn[2 * s + 1], v[1]);
+                atomicAdd(&Dn[2 * s], v[2]);
+                atomicAdd(&Dn[2 * s + 1], v[3]);
+                atomicAdd(&RDn[2 * s], v[4]);
+                atomicAdd(&RDn[2 * s + 1], v[5]);
+                wrows += (unsigned long long)run.frows;
+                wnnz += (unsigned long long)run.fnnz;
+            }
+        }
+        if (threadIdx.x == 0 && any) *(volatile unsigned*)&a.ACT[k % 3] = 1u;
+        grid.sync();
+        if (*(volatile unsigned*)&a.ACT[k % 3] == 0u) break;
+    }
+    if (threadIdx.x == 0) {
+        if (wrows) atomicAdd(&a.work[0], wrows);
+        if (wnnz) atomicAdd(&a.work[1], wnnz);
+        if (blockIdx.x == 0) a.out_iters[0] = k;
+    }
+}
+
 // Initial state of the dynamic schedule: converged flags from <r0, r0>, beta 0.
 __global__ void k_dyn_init(int nseg, int dncp, const double* __restrict__ RD0, const double* __restrict__ THR,
                            unsigned int* __restrict__ DONEF, double* __restrict__ BETA0) {
@@ -1179,6 +1387,18 @@ void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSyste
     const void* kern = D.minb == 3 ? (const void*)k_pcg_run<A, 3> : (const void*)k_pcg_run<A, 4>;
     PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RUN_THREADS, 0));
     if (per_sm <= 0) fail(PGCP_E_CUDA, "run-based PCG kernel cannot be resident");
+    if (D.sched == 4) {   // the single-reduction kernel shares the static row runs
+        int per_sm_cg1 = 0;
+        const void* kc = D.minb == 3 ? (const void*)k_pcg_cg1<A, 3> : (const void*)k_pcg_cg1<A, 4>;
+        PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cg1, kc, RUN_THREADS, 0));
+        if (per_sm_cg1 <= 0) fail(PGCP_E_CUDA, "single-reduction PCG kernel cannot be resident");
+        per_sm = std::min(per_sm, per_sm_cg1);
+        const size_t vbb = sizeof(typename A::V);
+        D.r1.alloc(n * vbb, s);
+        D.w0.alloc(n * vbb, s);
+        D.w1.alloc(n * vbb, s);
+        D.s1.alloc(n * vbb, s);
+    }
     D.per_sm = per_sm;
     int per_sm_dyn = 0;
     const void* kd = D.minb == 3 ? (const void*)k_pcg_dyn<A, 3> : (const void*)k_pcg_dyn<A, 4>;
@@ -1230,7 +1450,15 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     a.BETA = D.BETA.p;
     a.DONEF = D.DONEF.p;
     void* args[] = {(void*)&a};
-    if (D.sched == 2) {
+    a.r1 = reinterpret_cast<V*>(D.r1.p);
+    a.w0 = reinterpret_cast<V*>(D.w0.p);
+    a.w1 = reinterpret_cast<V*>(D.w1.p);
+    a.s1 = reinterpret_cast<V*>(D.s1.p);
+    a.DL = D.DL.p;
+    if (D.sched == 4) {
+        const void* kern = D.minb == 3 ? (const void*)k_pcg_cg1<A, 3> : (const void*)k_pcg_cg1<A, 4>;
+        { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(D.grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+    } else if (D.sched == 2) {
         const void* kern = D.minb == 3 ? (const void*)k_pcg_dyn<A, 3> : (const void*)k_pcg_dyn<A, 4>;
         const int grid = std::max(1, std::min(D.dyn_grid, D.nchunks));
         { PGCP_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(RUN_THREADS), args, 0, s)); ::pgcp::note_launch(); }
@@ -1266,7 +1494,7 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     if (bps != 0 && bps != 3 && bps != 4) fail(PGCP_E_ARG, "pcg_blocks_per_sm must be 0, 3 or 4");
     D.minb = bps == 3 ? 3 : 4;
     const int sched = ctx->opt.pcg_schedule;
-    if (sched < 0 || sched > 3) fail(PGCP_E_ARG, "pcg_schedule must be 0, 1, 2 or 3");
+    if (sched < 0 || sched > 4) fail(PGCP_E_ARG, "pcg_schedule must be 0 to 4");
     D.sched = sched == 0 ? 1 : sched;
     if (D.sched == 3 && P.K > RR_MAXSEG) D.sched = 1;   // the round-robin tables hold RR_MAXSEG pieces
     DBuf<int32_t> cnt;
@@ -1302,6 +1530,12 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     }
     roff[grid] = (int32_t)runs.size();
     D.nruns = (int32_t)runs.size();
+    if (D.sched == 4)
+        for (int b = 0; b < grid; ++b)
+            if (roff[b + 1] - roff[b] > CG1_MAXRUNS) {
+                D.sched = 1;   // more pieces per block than the kernel's run table: static schedule
+                break;
+            }
     D.runs.alloc(std::max<int64_t>(1, D.nruns), s);
     D.run_off.alloc(grid + 1, s);
     PGCP_CUDA(cudaMemcpyAsync(D.runs.p, runs.data(), runs.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
@@ -1338,8 +1572,9 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
         D.BETA.zero();
         PGCP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
     }
-    D.RR.alloc(3 * 2 * S, s);
-    D.RD.alloc(3 * 2 * S, s);
+    D.RR.alloc(4 * 2 * S, s);
+    D.RD.alloc(4 * 2 * S, s);
+    D.DL.alloc(4 * 2 * S, s);
     D.PQ.alloc(2 * 2 * S, s);
     D.ACT.alloc(3, s);
     D.THR.alloc(2 * S, s);
@@ -1355,6 +1590,7 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     const int S = P.K;
     D.RR.zero();
     D.RD.zero();
+    D.DL.zero();
     D.PQ.zero();
     D.ACT.zero();
     PGCP_CUDA(cudaMemcpyAsync(D.THR.p, thr.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));

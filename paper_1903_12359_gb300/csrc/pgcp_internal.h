@@ -233,12 +233,13 @@ struct DfSystem {
     DBuf<DfRun> runs;
     DBuf<int32_t> run_off;
     DBuf<unsigned char> x, r, p, q;   // n row pairs (float4 or float2)
-    DBuf<double> RR, RD, PQ, THR;
+    DBuf<unsigned char> r1, w0, w1, s1;   // single-reduction schedule only
+    DBuf<double> RR, RD, PQ, THR, DL;
     DBuf<unsigned int> ACT;
     DBuf<int32_t> out_it;
     DBuf<unsigned long long> work;
     // dynamic schedule: chunks inside pieces, per-piece chunk counts, counters
-    int sched = 1, dyn_grid = 0, rr_grid = 0;   // 1 static runs, 2 dynamic chunks, 3 round-robin chunks
+    int sched = 1, dyn_grid = 0, rr_grid = 0;   // 1 static runs, 2 dynamic, 3 round-robin, 4 single-reduction
     int32_t nchunks = 0;
     DBuf<DfRun> chunks;
     DBuf<int32_t> nch;

@@ -231,7 +231,7 @@ def test_partition_full_size_bit_exact(api):
     assert np.array_equal(loops, np.concatenate(P.loops))
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3], ids=["static", "dynamic", "roundrobin"])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4], ids=["static", "dynamic", "roundrobin", "onereduction"])
 @pytest.mark.parametrize("name", ["grid4x2", "sphere"])
 def test_dncp_and_final_under_every_pcg_schedule(api, name, schedule):
     """The three work schedules of the mixed-precision PCG give the oracle's map."""
