@@ -61,8 +61,8 @@ typedef struct {
     int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve */
     int32_t interior_map_fp64;/* 1: weld-map the interior in FP64 (else FP32) */
     int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
-    int32_t local_precision;  /* pgcp_precision of the DNCP solve (FP32_REFINED stalls: with two pins
-                                 its conditioning is beyond FP32 refinement) */
+    int32_t local_precision;  /* pgcp_precision of the DNCP solve: default DF64_REFINED (FP32_REFINED
+                                 stalls: with two pins the conditioning is beyond FP32 refinement) */
     int32_t spmv_lanes;       /* threads per matrix row in the FP64 PCG SpMV: 1, 2, 4 or 8 (autotuner
                                  output; 0 = default 1) */
     int32_t pcg_blocks_per_sm;/* resident 256-thread blocks per SM of the mixed-precision PCG kernel:

@@ -170,7 +170,7 @@ void pgcp_default_options(pgcp_options* o) {
     o->warm_start = PGCP_WARM_WELDMAP;
     o->interior_map_fp64 = 0;
     o->block_rows_log2 = 0;
-    o->local_precision = PGCP_FP64;
+    o->local_precision = PGCP_DF64_REFINED;
 }
 
 const char* pgcp_status_string(pgcp_status s) {
