@@ -325,7 +325,7 @@ def main():
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (burst copy)" if hbm else "fallback",
                 "traffic": (tr["dram_bytes_per_iteration"] * dncp_iters / max(pcg_launches, 1) if tr else None),
-                "traffic_note": (tr.get("note") if tr else "no ncu capture of the current pcg.cu"),
+                "traffic_note": (tr.get("note") if tr else "no ncu capture of the current kernel source"),
                 "algorithmic_bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
                 "avg_launch_ms": pcg_ms / max(pcg_launches, 1), "launches": pcg_launches,
                 "share_of_step": (pcg_ms / ms) if ms > 0 else None,
