@@ -73,7 +73,15 @@ typedef struct {
                                  pieces, else 1), 4 static with one reduction per iteration
                                  (Chronopoulos-Gear form; up to 16 pieces per block, else 1);
                                  autotuner output, 0 = default static */
-    int32_t reserved[3];
+    int32_t deterministic;    /* 1: every floating-point reduction that steers a solve (PCG dot products,
+                                 refinement residual norms, the learned start's scaling and check) is
+                                 summed in a fixed order, so repeated calls with the same inputs,
+                                 options and GPU model give bitwise identical results and iteration
+                                 counts.  The mixed-precision PCG then runs the static schedule.  Not
+                                 available with PGCP_FP64 in either solve stage (PGCP_E_ARG).
+                                 0 (default): unordered atomic sums, which may differ in the last
+                                 bits between runs and change the iteration count slightly. */
+    int32_t reserved[2];
 } pgcp_options;
 
 /* Per-call statistics (host struct, filled by pgcp_global_solve). */
@@ -92,8 +100,10 @@ typedef struct {
     int64_t n_copies;          /* sum of piece vertex counts */
     double  pcg_ms;            /* summed duration of the persistent PCG kernel launches (CUDA events
                                   on the context stream), both solve stages */
-    double  pcg_bytes;         /* algorithmic bytes those launches move: per active free row and
-                                  iteration 4 + 25*T, per stored entry of its row 4 + T (T = 4 or 8) */
+    double  pcg_bytes;         /* algorithmic bytes those launches move, per active free row and
+                                  iteration and per stored entry of its row: 8 + 22*T and 4 + T in the
+                                  mixed-precision kernels (T = 8 double-float, 4 FP32), 4 + 25*T and
+                                  4 + T in the FP64 kernel (T = 8) */
     int32_t pcg_launches;
     int32_t learned_pieces;    /* pieces whose final solve started from the learned prediction */
 } pgcp_stats;

@@ -536,8 +536,10 @@ pgcp_status pgcp_autotune(pgcp_ctx* ctx, pgcp_part* part, int32_t probe_iters, p
             for (int lanes : {1, 2, 4})
                 for (int rows : {8, 9, 10}) cands.push_back(Cand{saved.pcg_blocks_per_sm, saved.pcg_schedule, lanes, rows});
         } else {
+            // deterministic mode runs the static schedule only
             for (int sched : {1, 2, 3, 4})
-                for (int bps : {3, 4}) cands.push_back(Cand{bps, sched, saved.spmv_lanes, saved.block_rows_log2});
+                if (sched == 1 || !saved.deterministic)
+                    for (int bps : {3, 4}) cands.push_back(Cand{bps, sched, saved.spmv_lanes, saved.block_rows_log2});
         }
         double best = INFINITY;
         Cand pick = cands[0];

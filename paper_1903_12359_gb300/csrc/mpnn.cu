@@ -100,12 +100,13 @@ __global__ void k_mp_weights(int64_t n, const int32_t* __restrict__ rp, const in
     }
 }
 
-// z = -(1/d) L u on interior rows (FP64), per-piece sums of |z|^2 and counts
+// z = -(1/d) L u on interior rows (FP64), per-piece sums of |z|^2 and counts.
+// rowv (deterministic mode): |z_i|^2 per row instead of the atomic sums zz.
 __global__ void k_mp_z(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                        const double* __restrict__ val, const double* __restrict__ diag,
                        const uint8_t* __restrict__ is_bnd, const int32_t* __restrict__ row_piece,
                        const double2* __restrict__ u, float2* __restrict__ z, double* __restrict__ zz,
-                       unsigned long long* __restrict__ cnt) {
+                       unsigned long long* __restrict__ cnt, double* __restrict__ rowv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double s2 = 0.0;
     int inner = 0, piece = -1;
@@ -125,7 +126,9 @@ __global__ void k_mp_z(int64_t n, const int32_t* __restrict__ rp, const int32_t*
             inner = 1;
         }
         z[i] = make_float2((float)zi.x, (float)zi.y);
+        if (rowv) rowv[i] = s2;
     }
+    if (rowv) s2 = 0.0;
     // warp sums when the warp lies in one piece, else per lane
     const int lane = threadIdx.x & 31;
     const int p0 = __shfl_sync(0xffffffffu, piece, 0);
@@ -136,13 +139,30 @@ __global__ void k_mp_z(int64_t n, const int32_t* __restrict__ rp, const int32_t*
             inner += __shfl_xor_sync(0xffffffffu, inner, o);
         }
         if (lane == 0 && p0 >= 0 && inner > 0) {
-            atomicAdd(&zz[p0], s2);
+            if (!rowv) atomicAdd(&zz[p0], s2);
             atomicAdd(&cnt[p0], (unsigned long long)inner);
         }
     } else if (piece >= 0 && inner) {
-        atomicAdd(&zz[piece], s2);
+        if (!rowv) atomicAdd(&zz[piece], s2);
         atomicAdd(&cnt[piece], 1ull);
     }
+}
+
+// out[s] = sum of v over the rows [off[s], off[s+1]) of piece s in a fixed
+// order (deterministic mode): thread t adds rows t, t + 256, ... in sequence,
+// then a fixed halving tree.  One 256-thread block per piece.
+__global__ void k_seg_sum(const double* __restrict__ v, const int64_t* __restrict__ off, double* __restrict__ out) {
+    __shared__ double red[256];
+    const int s = blockIdx.x;
+    double a = 0.0;
+    for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += 256) a += v[i];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[s] = red[0];
 }
 
 __global__ void k_mp_sigma(int K, const double* __restrict__ zz, const unsigned long long* __restrict__ cnt,
@@ -315,11 +335,12 @@ __global__ void k_mp_apply(int64_t n, const double2* __restrict__ uw, const floa
     x[i] = u;
 }
 
-// per piece: sum over interior rows of |(L x)_i|^2 (FP64 Laplace residual)
+// per piece: sum over interior rows of |(L x)_i|^2 (FP64 Laplace residual);
+// rowv (deterministic mode): the row terms instead of the atomic sums
 __global__ void k_piece_residual(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                  const double* __restrict__ val, const uint8_t* __restrict__ is_bnd,
                                  const int32_t* __restrict__ row_piece, const double2* __restrict__ x,
-                                 double* __restrict__ rr) {
+                                 double* __restrict__ rr, double* __restrict__ rowv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double s2 = 0.0;
     int piece = -1;
@@ -335,7 +356,9 @@ __global__ void k_piece_residual(int64_t n, const int32_t* __restrict__ rp, cons
             s2 = ax * ax + ay * ay;
             if (!(s2 == s2)) s2 = INFINITY;   // NaN counts as no better
         }
+        if (rowv) rowv[i] = s2;
     }
+    if (rowv) return;
     const int p0 = __shfl_sync(0xffffffffu, piece, 0);
     if (__all_sync(0xffffffffu, piece == p0 || piece < 0)) {
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -386,8 +409,14 @@ void mp_inputs(pgcp_ctx* ctx, Part& P, MpWork& W, float* Ff) {
     W.sigma.alloc(P.K, s);
     W.zz.zero();
     W.cnt.zero();
+    DBuf<double> rowv;
+    if (ctx->opt.deterministic) rowv.alloc(n, s);
     { k_mp_z<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.diag64.p, P.is_bnd.p, P.row_piece.p,
-                                    P.welded.p, W.z.p, W.zz.p, W.cnt.p); ::pgcp::note_launch(); }
+                                    P.welded.p, W.z.p, W.zz.p, W.cnt.p, rowv.p); ::pgcp::note_launch(); }
+    if (ctx->opt.deterministic) {
+        k_seg_sum<<<(unsigned)P.K, 256, 0, s>>>(rowv.p, P.d_voff.p, W.zz.p);
+        ::pgcp::note_launch();
+    }
     { k_mp_sigma<<<nblk(P.K), 256, 0, s>>>(P.K, W.zz.p, W.cnt.p, W.sigma.p); ::pgcp::note_launch(); }
     W.F.alloc(n * FIN, s);
     { k_mp_feat<<<nblk(n), 256, 0, s>>>(n, W.z.p, W.sigma.p, P.row_piece.p, P.is_bnd.p,
@@ -558,10 +587,17 @@ int learned_start(pgcp_ctx* ctx, Part& P, double2* x) {
     rr.alloc(2 * P.K, s);
     use.alloc(P.K, s);
     rr.zero();
-    { k_piece_residual<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.is_bnd.p, P.row_piece.p, x,
-                                              rr.p); ::pgcp::note_launch(); }
-    { k_piece_residual<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.is_bnd.p, P.row_piece.p, xl.p,
-                                              rr.p + P.K); ::pgcp::note_launch(); }
+    DBuf<double> rowv;
+    const bool det = ctx->opt.deterministic != 0;
+    if (det) rowv.alloc(n, s);
+    for (int w = 0; w < 2; ++w) {
+        { k_piece_residual<<<nblk(n), 256, 0, s>>>(n, P.row_ptr.p, P.col.p, P.val64.p, P.is_bnd.p, P.row_piece.p,
+                                                  w ? xl.p : x, rr.p + w * P.K, rowv.p); ::pgcp::note_launch(); }
+        if (det) {
+            k_seg_sum<<<(unsigned)P.K, 256, 0, s>>>(rowv.p, P.d_voff.p, rr.p + w * P.K);
+            ::pgcp::note_launch();
+        }
+    }
     std::vector<double> h(2 * P.K);
     PGCP_CUDA(cudaMemcpyAsync(h.data(), rr.p, 2 * P.K * sizeof(double), cudaMemcpyDeviceToHost, s));
     PGCP_CUDA(cudaStreamSynchronize(s));

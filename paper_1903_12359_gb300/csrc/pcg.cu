@@ -352,8 +352,10 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> a) {
 // ---------------------------------------------------------------- helpers
 
 // Block sum of 4 doubles; thread 0 adds them to dst[0..3] (any may be null).
+// Block sums of four values; thread 0 adds them to d0..d3 (atomics), or, with
+// part, stores them at part[4 * blockIdx.x ...] for an ordered sum later.
 __device__ void block_add4(double v0, double v1, double v2, double v3, double* d0, double* d1, double* d2,
-                           double* d3) {
+                           double* d3, double* part = nullptr) {
     __shared__ double red[4 * 32];
     double v[4] = {v0, v1, v2, v3};
 #pragma unroll
@@ -369,6 +371,10 @@ __device__ void block_add4(double v0, double v1, double v2, double v3, double* d
         double sum[4] = {0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int i = 0; i < 4; ++i) sum[i] += red[4 * w + i];
+        if (part) {
+            for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = sum[i];
+            return;
+        }
         if (d0) atomicAdd(d0, sum[0]);
         if (d1) atomicAdd(d1, sum[1]);
         if (d2) atomicAdd(d2, sum[2]);
@@ -378,13 +384,15 @@ __device__ void block_add4(double v0, double v1, double v2, double v3, double* d
 
 // One block per tile: r = -(A x) on free rows (0 on fixed rows), and <r, r>
 // (and <r, D^-1 r>) per (piece, coordinate).  only_fixed: use x only at fixed
-// columns, which gives the right-hand side b of the free unknowns.
+// columns, which gives the right-hand side b of the free unknowns.  part:
+// per-tile sums instead of atomics (deterministic mode).
 template <typename TM, typename TX>
 __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __restrict__ rp,
                            const int32_t* __restrict__ col, const TM* __restrict__ val,
                            const double* __restrict__ dinv64, const int2* __restrict__ nb, int dncp,
                            const TX* __restrict__ x, int only_fixed, double2* __restrict__ r_out,
-                           double* __restrict__ RR, double* __restrict__ RZ, double2* __restrict__ z_out = nullptr) {
+                           double* __restrict__ RR, double* __restrict__ RZ, double2* __restrict__ z_out = nullptr,
+                           double* __restrict__ part = nullptr) {
     const Tile t = tiles[blockIdx.x];
     double a0 = 0, a1 = 0, z0 = 0, z1 = 0;
     for (int i = t.lo + threadIdx.x; i < t.hi; i += blockDim.x) {
@@ -422,7 +430,7 @@ __global__ void k_residual(const Tile* __restrict__ tiles, const int32_t* __rest
     }
     const int s = t.seg;
     block_add4(a0, a1, z0, z1, RR ? &RR[2 * s] : nullptr, RR ? &RR[2 * s + 1] : nullptr,
-               RZ ? &RZ[2 * s] : nullptr, RZ ? &RZ[2 * s + 1] : nullptr);
+               RZ ? &RZ[2 * s] : nullptr, RZ ? &RZ[2 * s + 1] : nullptr, part);
 }
 
 __global__ void k_tile_stats(Tile* tiles, const int32_t* __restrict__ rp, const uint8_t* __restrict__ fixed) {
@@ -483,25 +491,21 @@ void launch_pcg(pgcp_ctx* ctx, const PcgArgs<T>& a, int* grid_out) {
 template <typename T>
 void launch_pcg_lanes(pgcp_ctx* ctx, Part& P, PcgArgs<T> a) {
     int grid = 0;
-    cudaEvent_t e0, e1;
-    PGCP_CUDA(cudaEventCreate(&e0));
-    PGCP_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
     PGCP_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), ctx->stream));
-    PGCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    PGCP_CUDA(cudaEventRecord(ev.a, ctx->stream));
     switch (a.lanes) {
         case 2: launch_pcg<T, 2>(ctx, a, &grid); break;
         case 4: launch_pcg<T, 4>(ctx, a, &grid); break;
         case 8: launch_pcg<T, 8>(ctx, a, &grid); break;
         default: a.lanes = 1; launch_pcg<T, 1>(ctx, a, &grid); break;
     }
-    PGCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    PGCP_CUDA(cudaEventRecord(ev.b, ctx->stream));
     unsigned long long w[2] = {0, 0};
     PGCP_CUDA(cudaMemcpyAsync(w, a.work, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
-    PGCP_CUDA(cudaEventSynchronize(e1));
+    PGCP_CUDA(cudaEventSynchronize(ev.b));
     float ms = 0.f;
-    PGCP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    PGCP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
     const double Tb = (double)sizeof(T);
     P.stats.pcg_ms += ms;
     // per free row and iteration: row pointer 4 B, inverse diagonal T (phase 2),
@@ -521,6 +525,9 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     cudaStream_t s = ctx->stream;
     pgcp_options o = ctx->opt;
     if (dncp) o.precision = o.local_precision;
+    if (o.deterministic != 0 && o.deterministic != 1) fail(PGCP_E_ARG, "deterministic must be 0 or 1");
+    if (o.deterministic && o.precision == PGCP_FP64)
+        fail(PGCP_E_ARG, "deterministic mode needs a mixed-precision solver (FP32_REFINED or DF64_REFINED)");
     const int64_t n = P.Nc;
     const int S = P.K;
     // tiles: rows of one piece, at most 2^log2 rows each
@@ -556,12 +563,35 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
     out_it.alloc(1, s);
     BB.zero();
     const unsigned nt = (unsigned)tiles.size();
+    // deterministic mode: the residual kernels store per-tile sums, added here
+    // on the host in tile order (tiles run through the pieces in order)
+    const bool det = o.deterministic != 0;
+    DBuf<double> TP;
+    std::vector<double> hTP;
+    if (det) {
+        TP.alloc(4 * (int64_t)nt, s);
+        hTP.resize(4 * (size_t)nt);
+    }
+    double* const tp = det ? TP.p : nullptr;
+    auto fetch = [&](const DBuf<double>& acc, std::vector<double>& h) {
+        if (!det) {
+            PGCP_CUDA(cudaMemcpyAsync(h.data(), acc.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
+            PGCP_CUDA(cudaStreamSynchronize(s));
+            return;
+        }
+        PGCP_CUDA(cudaMemcpyAsync(hTP.data(), TP.p, hTP.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PGCP_CUDA(cudaStreamSynchronize(s));
+        std::fill(h.begin(), h.end(), 0.0);
+        for (size_t t = 0; t < tiles.size(); ++t) {
+            h[2 * tiles[t].seg] += hTP[4 * t];
+            h[2 * tiles[t].seg + 1] += hTP[4 * t + 1];
+        }
+    };
     { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p, P.nb.p,
-                                                  dncp, x, 1, nullptr, BB.p, nullptr); ::pgcp::note_launch(); }
+                                                  dncp, x, 1, nullptr, BB.p, nullptr, nullptr, tp); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     std::vector<double> hBB(2 * S), hRR(2 * S), hTHR(2 * S);
-    PGCP_CUDA(cudaMemcpyAsync(hBB.data(), BB.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-    PGCP_CUDA(cudaStreamSynchronize(s));
+    fetch(BB, hBB);
     SolveResult res;
     const double tol2 = o.tol * o.tol;
     auto relres_of = [&](const std::vector<double>& rr, bool* all_ok) {
@@ -593,9 +623,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
             RRo.zero();
             { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                          P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr); ::pgcp::note_launch(); }
-            PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-            PGCP_CUDA(cudaStreamSynchronize(s));
+                                                          P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr, nullptr, tp); ::pgcp::note_launch(); }
+            fetch(RRo, hRR);
             bool ok = false;
             res.relres = relres_of(hRR, &ok);
             res.refine = outer;
@@ -617,9 +646,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         }
         RRo.zero();
         { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
-        PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PGCP_CUDA(cudaStreamSynchronize(s));
+                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr, nullptr, tp); ::pgcp::note_launch(); }
+        fetch(RRo, hRR);
         bool ok = false;
         res.relres = relres_of(hRR, &ok);
         res.refine = std::max(1, o.max_refine);
@@ -661,9 +689,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         }
         RRo.zero();
         { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
-                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr); ::pgcp::note_launch(); }
-        PGCP_CUDA(cudaMemcpyAsync(hRR.data(), RRo.p, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PGCP_CUDA(cudaStreamSynchronize(s));
+                                                      P.nb.p, dncp, x, 0, nullptr, RRo.p, nullptr, nullptr, tp); ::pgcp::note_launch(); }
+        fetch(RRo, hRR);
         bool ok = false;
         res.relres = relres_of(hRR, &ok);
         res.refine = std::max(1, o.max_refine);

@@ -168,7 +168,42 @@ struct RunArgs {
     double* ALPHA;                      // [2][2 nseg]
     double* BETA;                       // [2][2 nseg]
     unsigned int* DONEF;                // [2 nseg] coordinate converged (monotonic)
+    // deterministic mode (static schedule): every run stores its partial sums,
+    // and a piece's total is summed over its runs in run order where needed
+    int32_t det;
+    int32_t nruns;
+    const int32_t* __restrict__ prun;   // [2 nseg] first and one-past-last run of each piece
+    double* PRR;                        // [3][nruns][2] scaled <r, r> per run
+    double* PRD;                        // [3][nruns][2] unscaled sum d r^2 per run
+    double* PPQ;                        // [2][nruns][2] <p, q> per run
+    int32_t* RDONE;                     // [nruns][2] coordinate converged (set once, by the run's block)
+    double* CRR;                        // [nruns][2] the piece's scaled <r, r> of the latest phase B
 };
+
+// NQ sums of src[q][2 i] over the runs i in [r0, r1), in a fixed order: lane l
+// adds runs r0 + l, r0 + l + 32, ... in sequence, then a butterfly over the
+// lanes.  IEEE addition is commutative, so every lane ends with the same bits,
+// and every warp that sums the same runs gets the same totals.  The NQ loads
+// of a step are issued together.  Full warp.
+template <int NQ>
+__device__ __forceinline__ void ordered_sums(const double* const* src, int r0, int r1, double* out) {
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+    for (int i = r0 + (int)(threadIdx.x & 31); i < r1; i += 32) {
+        double t[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) t[q] = __ldcg(src[q] + 2 * i);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] += t[q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = v[q];
+}
 
 // Accumulators written by other blocks (atomics, then a grid sync) are read
 // through L2 (__ldcg): another SM's L1 may hold an older line.
@@ -264,7 +299,51 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
         for (int ri = rb; ri < re; ++ri) {
             const DfRun run = a.runs[ri];
             const int s = run.seg, slot = ri & 1;
-            if (threadIdx.x == 0) {
+            if (a.det) {
+                if (threadIdx.x < 32) {   // warp 0: ordered sums over the piece's runs
+                    const int r0 = a.prun[2 * s], r1 = a.prun[2 * s + 1], nr2 = 2 * a.nruns;
+                    bool d0 = __ldcg(a.RDONE + 2 * ri) != 0, d1 = __ldcg(a.RDONE + 2 * ri + 1) != 0;
+                    double b0 = 0.0, b1 = 0.0, t[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (!(d0 && d1)) {
+                        // this iteration's sum d r^2 and <r, r>; the previous <r, r> is cached
+                        const double* PRDk = a.PRD + (k % 3) * nr2;
+                        const double* PRRk = a.PRR + (k % 3) * nr2;
+                        const double* src[4] = {PRDk, PRDk + 1, PRRk, PRRk + 1};
+                        ordered_sums<4>(src, r0, r1, t);
+                        if (a.dncp) {
+                            const bool dn = t[0] + t[1] <= a.THR[2 * s] + a.THR[2 * s + 1];
+                            d0 = d0 || dn;
+                            d1 = d1 || dn;
+                        } else {
+                            d0 = d0 || t[0] <= a.THR[2 * s];
+                            d1 = d1 || t[1] <= a.THR[2 * s + 1];
+                        }
+                        if (k > 0 && !(d0 && d1)) {
+                            const double m0 = __ldcg(a.CRR + 2 * ri), m1 = __ldcg(a.CRR + 2 * ri + 1);
+                            if (a.dncp) {
+                                const double num = t[2] + t[3], den = m0 + m1;
+                                b0 = b1 = den > 0.0 ? num / den : 0.0;
+                            } else {
+                                b0 = m0 > 0.0 ? t[2] / m0 : 0.0;
+                                b1 = m1 > 0.0 ? t[3] / m1 : 0.0;
+                            }
+                        }
+                    }
+                    __syncwarp();   // every lane has read CRR before lane 0 replaces it
+                    if (threadIdx.x == 0) {
+                        if (!(d0 && d1)) {
+                            a.CRR[2 * ri] = t[2];
+                            a.CRR[2 * ri + 1] = t[3];
+                        }
+                        if (d0) a.RDONE[2 * ri] = 1;
+                        if (d1) a.RDONE[2 * ri + 1] = 1;
+                        sc[slot][0] = b0;
+                        sc[slot][1] = b1;
+                        sflag[slot][0] = d0;
+                        sflag[slot][1] = d1;
+                    }
+                }
+            } else if (threadIdx.x == 0) {
                 const bool d0 = piece_done(RDk, a.THR, s, 0, a.dncp);
                 const bool d1 = piece_done(RDk, a.THR, s, 1, a.dncp);
                 double b0 = 0.0, b1 = 0.0;
@@ -348,8 +427,14 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
             double v[2];
             block_sum_df<2>(pv, red, v);
             if (threadIdx.x == 0) {
-                atomicAdd(&PQk[2 * s], v[0]);
-                atomicAdd(&PQk[2 * s + 1], v[1]);
+                if (a.det) {
+                    double* o = a.PPQ + (k % 2) * 2 * a.nruns + 2 * ri;
+                    o[0] = v[0];
+                    o[1] = v[1];
+                } else {
+                    atomicAdd(&PQk[2 * s], v[0]);
+                    atomicAdd(&PQk[2 * s + 1], v[1]);
+                }
                 wrows += (unsigned long long)run.frows;
                 wnnz += (unsigned long long)run.fnnz;
             }
@@ -367,7 +452,34 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
         for (int ri = rb; ri < re; ++ri) {
             const DfRun run = a.runs[ri];
             const int s = run.seg, slot = ri & 1;
-            if (threadIdx.x == 0) {
+            if (a.det) {
+                if (threadIdx.x < 32) {   // warp 0; the converged flags are phase B's of this iteration
+                    const int r0 = a.prun[2 * s], r1 = a.prun[2 * s + 1], nr2 = 2 * a.nruns;
+                    const bool d0 = __ldcg(a.RDONE + 2 * ri) != 0, d1 = __ldcg(a.RDONE + 2 * ri + 1) != 0;
+                    double al0 = 0.0, al1 = 0.0;
+                    if (!(d0 && d1)) {
+                        // <r, r> of this iteration from phase B's cache; <p, q> summed now
+                        const double n0 = __ldcg(a.CRR + 2 * ri), n1 = __ldcg(a.CRR + 2 * ri + 1);
+                        const double* PPQk = a.PPQ + (k % 2) * nr2;
+                        const double* src[2] = {PPQk, PPQk + 1};
+                        double t[2];
+                        ordered_sums<2>(src, r0, r1, t);
+                        const double q0 = t[0], q1 = t[1];
+                        if (a.dncp) {
+                            const double den = q0 + q1;
+                            al0 = al1 = den > 0.0 ? (n0 + n1) / den : 0.0;
+                        } else {
+                            if (!d0) al0 = q0 > 0.0 ? n0 / q0 : 0.0;
+                            if (!d1) al1 = q1 > 0.0 ? n1 / q1 : 0.0;
+                        }
+                    }
+                    if (threadIdx.x == 0) {
+                        sc[slot][0] = al0;
+                        sc[slot][1] = al1;
+                        sflag[slot][0] = d0 && d1;
+                    }
+                }
+            } else if (threadIdx.x == 0) {
                 const bool d0 = piece_done(RDk, a.THR, s, 0, a.dncp);
                 const bool d1 = piece_done(RDk, a.THR, s, 1, a.dncp);
                 double al0 = 0.0, al1 = 0.0;
@@ -413,7 +525,14 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
             float2 pv[4] = {A::as_df(rr0), A::as_df(rr1), make_float2(rd0, 0.f), make_float2(rd1, 0.f)};
             double v[4];
             block_sum_df<4>(pv, red, v);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && a.det) {
+                double* o = a.PRR + ((k + 1) % 3) * 2 * a.nruns + 2 * ri;
+                double* d = a.PRD + ((k + 1) % 3) * 2 * a.nruns + 2 * ri;
+                o[0] = v[0];
+                o[1] = v[1];
+                d[0] = v[2];
+                d[1] = v[3];
+            } else if (threadIdx.x == 0) {
                 atomicAdd(&RRn[2 * s], v[0]);
                 atomicAdd(&RRn[2 * s + 1], v[1]);
                 atomicAdd(&RDn[2 * s], v[2]);
@@ -1324,7 +1443,8 @@ template <typename A>
 __global__ void k_run_prep(const DfRun* __restrict__ runs, const int32_t* __restrict__ run_off,
                            const double2* __restrict__ r64, const double* __restrict__ sc, typename A::V* __restrict__ x,
                            typename A::V* __restrict__ r, typename A::V* __restrict__ p, typename A::V* __restrict__ q,
-                           double* __restrict__ RR, double* __restrict__ RD) {
+                           double* __restrict__ RR, double* __restrict__ RD, double* __restrict__ PRR0,
+                           double* __restrict__ PRD0) {
     __shared__ double red[4 * (RUN_THREADS / 32)];
     for (int ri = run_off[blockIdx.x]; ri < run_off[blockIdx.x + 1]; ++ri) {
         const DfRun run = runs[ri];
@@ -1348,7 +1468,12 @@ __global__ void k_run_prep(const DfRun* __restrict__ runs, const int32_t* __rest
             }
         }
         block_sum64<4>(v, red);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && PRR0) {   // deterministic mode: per-run sums
+            PRR0[2 * ri] = v[0];
+            PRR0[2 * ri + 1] = v[1];
+            PRD0[2 * ri] = v[2];
+            PRD0[2 * ri + 1] = v[3];
+        } else if (threadIdx.x == 0) {
             atomicAdd(&RR[2 * run.seg], v[0]);
             atomicAdd(&RR[2 * run.seg + 1], v[1]);
             atomicAdd(&RD[2 * run.seg], v[2]);
@@ -1426,7 +1551,8 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     V* pv = reinterpret_cast<V*>(D.p.p);
     V* qv = reinterpret_cast<V*>(D.q.p);
     { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, D.RR.p,
-                                                            D.RD.p); ::pgcp::note_launch(); }
+                                                            D.RD.p, D.det ? D.PRR.p : nullptr,
+                                                            D.det ? D.PRD.p : nullptr); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     if (D.sched >= 2) {
         { k_dyn_init<<<(unsigned)std::max<int64_t>(1, ceil_div((int64_t)P.K, 256)), 256, 0, s>>>(
@@ -1449,6 +1575,14 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
     a.ALPHA = D.ALPHA.p;
     a.BETA = D.BETA.p;
     a.DONEF = D.DONEF.p;
+    a.det = D.det;
+    a.nruns = D.nruns;
+    a.prun = D.prun.p;
+    a.PRR = D.PRR.p;
+    a.PRD = D.PRD.p;
+    a.PPQ = D.PPQ.p;
+    a.RDONE = D.RDONE.p;
+    a.CRR = D.CRR.p;
     void* args[] = {(void*)&a};
     a.r1 = reinterpret_cast<V*>(D.r1.p);
     a.w0 = reinterpret_cast<V*>(D.w0.p);
@@ -1496,6 +1630,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     const int sched = ctx->opt.pcg_schedule;
     if (sched < 0 || sched > 4) fail(PGCP_E_ARG, "pcg_schedule must be 0 to 4");
     D.sched = sched == 0 ? 1 : sched;
+    D.det = ctx->opt.deterministic ? 1 : 0;
+    if (D.det) D.sched = 1;   // ordered sums are implemented for the static schedule
     if (D.sched == 3 && P.K > RR_MAXSEG) D.sched = 1;   // the round-robin tables hold RR_MAXSEG pieces
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;
@@ -1538,6 +1674,20 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
             }
     D.runs.alloc(std::max<int64_t>(1, D.nruns), s);
     D.run_off.alloc(grid + 1, s);
+    // runs of a piece are consecutive (blocks and their runs follow the rows)
+    std::vector<int32_t> prun(2 * (size_t)std::max(1, P.K), 0);
+    for (int32_t i = (int32_t)runs.size() - 1; i >= 0; --i) prun[2 * runs[i].seg] = i;
+    for (int32_t i = 0; i < (int32_t)runs.size(); ++i) prun[2 * runs[i].seg + 1] = i + 1;
+    if (D.det) {
+        D.prun.alloc(prun.size(), s);
+        PGCP_CUDA(cudaMemcpyAsync(D.prun.p, prun.data(), prun.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        const int64_t nr = std::max<int64_t>(1, D.nruns);
+        D.PRR.alloc(3 * 2 * nr, s);
+        D.PRD.alloc(3 * 2 * nr, s);
+        D.PPQ.alloc(2 * 2 * nr, s);
+        D.RDONE.alloc(2 * nr, s);
+        D.CRR.alloc(2 * nr, s);
+    }
     PGCP_CUDA(cudaMemcpyAsync(D.runs.p, runs.data(), runs.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
     PGCP_CUDA(cudaMemcpyAsync(D.run_off.p, roff.data(), roff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (D.nruns > 0) {
@@ -1593,15 +1743,19 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     D.DL.zero();
     D.PQ.zero();
     D.ACT.zero();
+    if (D.det) {
+        D.PRR.zero();
+        D.PRD.zero();
+        D.PPQ.zero();
+        D.RDONE.zero();
+    }
     PGCP_CUDA(cudaMemcpyAsync(D.THR.p, thr.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
     PGCP_CUDA(cudaMemsetAsync(D.work.p, 0, 2 * sizeof(unsigned long long), s));
-    cudaEvent_t e0, e1;
-    PGCP_CUDA(cudaEventCreate(&e0));
-    PGCP_CUDA(cudaEventCreate(&e1));
-    // the event pair brackets the persistent kernel only (e0 follows the prep kernel)
-    if (D.f32) solve_typed<ArithF32>(ctx, P, D, r64, max_iters, e0);
-    else solve_typed<ArithDF>(ctx, P, D, r64, max_iters, e0);
-    PGCP_CUDA(cudaEventRecord(e1, s));
+    EventPair ev;
+    // the event pair brackets the persistent kernel only (ev.a follows the prep kernel)
+    if (D.f32) solve_typed<ArithF32>(ctx, P, D, r64, max_iters, ev.a);
+    else solve_typed<ArithDF>(ctx, P, D, r64, max_iters, ev.a);
+    PGCP_CUDA(cudaEventRecord(ev.b, s));
     if (D.f32) finish_typed<ArithF32>(ctx, D, x);
     else finish_typed<ArithDF>(ctx, D, x);
     unsigned long long w[2] = {0, 0};
@@ -1610,9 +1764,7 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     PGCP_CUDA(cudaMemcpyAsync(&it, D.out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     PGCP_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
-    PGCP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    PGCP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
     P.stats.pcg_ms += ms;
     // Per free row and iteration, with vector pairs of 2T bytes (T = 8 for
     // double-float, 4 for FP32): phase B row pointer 4, r 2T, p r/w 4T,

@@ -39,6 +39,26 @@ enum DevErr : uint32_t {
     DE_TIMEOUT = 1u << 9,      // a bounded wait in a kernel gave up
 };
 
+// Two CUDA events, destroyed on scope exit (also when a failing call throws).
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EventPair() {
+        PGCP_CUDA(cudaEventCreate(&a));
+        const cudaError_t e = cudaEventCreate(&b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            a = nullptr;
+            check_cuda(e, "cudaEventCreate");
+        }
+    }
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    EventPair(const EventPair&) = delete;
+    EventPair& operator=(const EventPair&) = delete;
+};
+
 // ------------------------------------------------------------------ device memory
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on one stream).
@@ -245,6 +265,10 @@ struct DfSystem {
     DBuf<int32_t> nch;
     DBuf<unsigned int> CTR, CNTB, CNTA, DONEF;
     DBuf<double> ALPHA, BETA;
+    // deterministic mode: per-run partial sums and converged flags, run range per piece
+    int det = 0;
+    DBuf<int32_t> prun, RDONE;
+    DBuf<double> PRR, PRD, PPQ, CRR;
 };
 void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D);
 // One inner solve of A d = r64 (thresholds on the unscaled <r, r> per piece

@@ -39,3 +39,35 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof and field offsets of the option, statistics and distortion structs
+    as a C compiler lays them out from include/pgcp.h, against the ctypes
+    binding (a stale binding would pass garbage through the ABI)."""
+    import shutil
+    import subprocess
+    from paper_1903_12359_gb300 import api
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pgcp_options": api.Options, "pgcp_stats": api.Stats, "pgcp_distortion": api.Distortion,
+               "pgcp_mesh_desc": api.MeshDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pgcp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for ln in filter(None, got):
+        cname, what, val = ln.split()
+        py = structs[cname]
+        want = ctypes.sizeof(py) if what == "size" else getattr(py, what).offset
+        assert int(val) == want, (cname, what, int(val), want)
+    o = api.default_options()
+    assert o.deterministic == 0 and o.local_precision == api.DF64_REFINED
