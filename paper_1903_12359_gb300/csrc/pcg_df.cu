@@ -125,6 +125,9 @@ struct ArithF32 {
 };
 
 constexpr int RUN_THREADS = 256;
+// Iterations per launch of a static-schedule solve; the runs are rebuilt over
+// the unconverged pieces between launches (see df_solve).
+constexpr int REBALANCE_ITERS = 1024;
 // Resident blocks per SM the kernel is compiled for (MINB): 4 caps it at 64
 // registers (32 warps per SM), 3 at 80 (24 warps, no spills in double-float).
 
@@ -168,6 +171,9 @@ struct RunArgs {
     double* ALPHA;                      // [2][2 nseg]
     double* BETA;                       // [2][2 nseg]
     unsigned int* DONEF;                // [2 nseg] coordinate converged (monotonic)
+    // static schedule: first iteration of this launch (a solve may run as several
+    // launches, the later ones over the rows of the unconverged pieces only)
+    int32_t k0;
     // deterministic mode (static schedule): every run stores its partial sums,
     // and a piece's total is summed over its runs in run order where needed
     int32_t det;
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
     const S* __restrict__ valp = a.val;
     const float* __restrict__ dgp = a.dgn;
     unsigned long long wrows = 0, wnnz = 0;
-    int k = 0;
+    int k = a.k0;
     for (; k < a.max_iters; ++k) {
         const double* RRk = a.RR + (k % 3) * 2 * nseg;
         const double* RRm = a.RR + ((k + 2) % 3) * 2 * nseg;
@@ -1543,7 +1549,7 @@ void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSyste
 }
 
 template <typename A>
-void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int max_iters, cudaEvent_t e0) {
+void prep_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64) {
     cudaStream_t s = ctx->stream;
     using V = typename A::V;
     V* xv = reinterpret_cast<V*>(D.x.p);
@@ -1562,10 +1568,22 @@ void solve_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int ma
         D.CNTA.zero();
         PGCP_CUDA(cudaGetLastError());
     }
-    PGCP_CUDA(cudaEventRecord(e0, s));
+}
+
+// One persistent launch: iterations k0 .. cap - 1 (it stops earlier once every
+// piece has converged; out_it then holds the iteration it stopped at).
+template <typename A>
+void launch_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap) {
+    cudaStream_t s = ctx->stream;
+    using V = typename A::V;
+    V* xv = reinterpret_cast<V*>(D.x.p);
+    V* rv = reinterpret_cast<V*>(D.r.p);
+    V* pv = reinterpret_cast<V*>(D.p.p);
+    V* qv = reinterpret_cast<V*>(D.q.p);
     RunArgs<A> a{(int32_t)D.n, P.K, D.rp.p, D.col.p, reinterpret_cast<const typename A::S*>(D.val.p), D.dgn.p, xv, rv,
-                 pv, qv, D.runs.p, D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, max_iters,
+                 pv, qv, D.runs.p, D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, cap,
                  D.dncp, D.work.p};
+    a.k0 = k0;
     a.chunks = D.chunks.p;
     a.nchunks = D.nchunks;
     a.nch = D.nch.p;
@@ -1617,6 +1635,43 @@ void finish_typed(pgcp_ctx* ctx, DfSystem& D, double2* x) {
 
 // ---------------------------------------------------------------- host side
 
+// Row runs of the persistent grid: the rows of the active pieces (all when
+// active is null), concatenated in piece order, split into `grid` equal ranges,
+// each range cut at piece boundaries.  Returns the rows covered.
+int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* active, int grid,
+                  std::vector<DfRun>& runs, std::vector<int32_t>& roff) {
+    std::vector<int> segs;
+    int64_t total = 0;
+    for (int i = 0; i + 1 < (int)voff.size(); ++i)
+        if (!active || (*active)[i]) {
+            segs.push_back(i);
+            total += voff[i + 1] - voff[i];
+        }
+    runs.clear();
+    roff.assign(grid + 1, 0);
+    size_t c = 0;
+    int64_t pos = 0, cbase = 0;   // position in the concatenation; start of piece segs[c] in it
+    for (int b = 0; b < grid; ++b) {
+        roff[b] = (int32_t)runs.size();
+        const int64_t target = total * (b + 1) / grid;
+        while (pos < target && c < segs.size()) {
+            const int seg = segs[c];
+            const int64_t len = voff[seg + 1] - voff[seg];
+            const int64_t end = std::min<int64_t>(target, cbase + len);
+            if (end > pos)
+                runs.push_back(DfRun{seg, (int32_t)(voff[seg] + (pos - cbase)), (int32_t)(voff[seg] + (end - cbase)), 0, 0,
+                                     0, 0, 0});
+            pos = end;
+            if (pos == cbase + len) {
+                cbase += len;
+                ++c;
+            }
+        }
+    }
+    roff[grid] = (int32_t)runs.size();
+    return total;
+}
+
 void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D) {
     cudaStream_t s = ctx->stream;
     const int64_t n = P.Nc;
@@ -1653,18 +1708,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     grid = std::max(grid, 1);
     D.grid = grid;
     std::vector<DfRun> runs;
-    std::vector<int32_t> roff(grid + 1, 0);
-    for (int b = 0; b < grid; ++b) {
-        int64_t lo = n * b / grid, hi = n * (b + 1) / grid;
-        roff[b] = (int32_t)runs.size();
-        while (lo < hi) {
-            const int seg = (int)(std::upper_bound(P.voff.begin(), P.voff.end(), lo) - P.voff.begin()) - 1;
-            const int64_t end = std::min<int64_t>(hi, P.voff[seg + 1]);
-            runs.push_back(DfRun{seg, (int32_t)lo, (int32_t)end, 0, 0, 0, 0, 0});
-            lo = end;
-        }
-    }
-    roff[grid] = (int32_t)runs.size();
+    std::vector<int32_t> roff;
+    D.covered = make_runs(P.voff, nullptr, grid, runs, roff);
     D.nruns = (int32_t)runs.size();
     if (D.sched == 4)
         for (int b = 0; b < grid; ++b)
@@ -1672,7 +1717,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
                 D.sched = 1;   // more pieces per block than the kernel's run table: static schedule
                 break;
             }
-    D.runs.alloc(std::max<int64_t>(1, D.nruns), s);
+    D.runs_cap = std::max<int64_t>(D.nruns, (int64_t)grid + P.K);   // room for the rebuilt runs
+    D.runs.alloc(std::max<int64_t>(1, D.runs_cap), s);
     D.run_off.alloc(grid + 1, s);
     // runs of a piece are consecutive (blocks and their runs follow the rows)
     std::vector<int32_t> prun(2 * (size_t)std::max(1, P.K), 0);
@@ -1751,28 +1797,84 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     }
     PGCP_CUDA(cudaMemcpyAsync(D.THR.p, thr.data(), 2 * S * sizeof(double), cudaMemcpyHostToDevice, s));
     PGCP_CUDA(cudaMemsetAsync(D.work.p, 0, 2 * sizeof(unsigned long long), s));
-    EventPair ev;
-    // the event pair brackets the persistent kernel only (ev.a follows the prep kernel)
-    if (D.f32) solve_typed<ArithF32>(ctx, P, D, r64, max_iters, ev.a);
-    else solve_typed<ArithDF>(ctx, P, D, r64, max_iters, ev.a);
-    PGCP_CUDA(cudaEventRecord(ev.b, s));
+    // a previous solve may have left runs over some pieces only: every solve
+    // starts (and its prep kernel runs) over all rows
+    auto set_runs = [&](const std::vector<uint8_t>* active) {
+        std::vector<DfRun> runs;
+        std::vector<int32_t> roff;
+        D.covered = make_runs(P.voff, active, D.grid, runs, roff);
+        if ((int64_t)runs.size() > D.runs_cap) fail(PGCP_E_CUDA, "rebuilt PCG runs exceed their buffer");
+        D.nruns = (int32_t)runs.size();
+        PGCP_CUDA(cudaMemcpyAsync(D.runs.p, runs.data(), runs.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
+        PGCP_CUDA(cudaMemcpyAsync(D.run_off.p, roff.data(), roff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (D.nruns > 0) {
+            k_run_stats<<<(unsigned)D.nruns, 256, 0, s>>>(D.runs.p, D.rp.p);
+            ::pgcp::note_launch();
+        }
+        PGCP_CUDA(cudaGetLastError());
+        PGCP_CUDA(cudaStreamSynchronize(s));   // the host run lists go out of scope
+    };
+    if (D.covered != D.n) set_runs(nullptr);
+    if (D.f32) prep_typed<ArithF32>(ctx, P, D, r64);
+    else prep_typed<ArithDF>(ctx, P, D, r64);
+    auto launch = [&](int k0, int cap) {
+        EventPair ev;   // brackets the persistent kernel only
+        PGCP_CUDA(cudaEventRecord(ev.a, s));
+        if (D.f32) launch_typed<ArithF32>(ctx, P, D, k0, cap);
+        else launch_typed<ArithDF>(ctx, P, D, k0, cap);
+        PGCP_CUDA(cudaEventRecord(ev.b, s));
+        int k_end = 0;
+        PGCP_CUDA(cudaMemcpyAsync(&k_end, D.out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PGCP_CUDA(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        PGCP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        P.stats.pcg_ms += ms;
+        P.stats.pcg_launches += 1;
+        return k_end;
+    };
+    int it = 0;
+    if (D.sched == 1 && !D.det) {
+        // Static schedule: the solve runs in launches of REBALANCE_ITERS
+        // iterations.  Between them the host reads which pieces converged;
+        // when the rows of the others fall below 3/4 of the rows the runs
+        // cover, the runs are rebuilt over those rows alone, so the remaining
+        // pieces spread over every block again.  The per-piece accumulators
+        // and vectors carry over, and the iteration index continues.
+        std::vector<double> rd(2 * (size_t)S);
+        std::vector<uint8_t> active(S, 1);
+        while (true) {
+            const int cap = (int)std::min<int64_t>(max_iters, (int64_t)it + REBALANCE_ITERS);
+            const int k_end = launch(it, cap);
+            const bool stopped = k_end < cap;   // every piece converged
+            it = k_end;
+            if (stopped || it >= max_iters) break;
+            PGCP_CUDA(cudaMemcpyAsync(rd.data(), D.RD.p + (it % 3) * 2 * S, 2 * S * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+            PGCP_CUDA(cudaStreamSynchronize(s));
+            int64_t rows = 0;
+            for (int i = 0; i < S; ++i) {
+                bool done;
+                if (D.dncp) done = rd[2 * i] + rd[2 * i + 1] <= thr[2 * i] + thr[2 * i + 1];
+                else done = rd[2 * i] <= thr[2 * i] && rd[2 * i + 1] <= thr[2 * i + 1];
+                active[i] = done ? 0 : 1;
+                if (!done) rows += P.voff[i + 1] - P.voff[i];
+            }
+            if (rows > 0 && 4 * rows < 3 * D.covered) set_runs(&active);
+        }
+    } else {
+        it = launch(0, max_iters);
+    }
     if (D.f32) finish_typed<ArithF32>(ctx, D, x);
     else finish_typed<ArithDF>(ctx, D, x);
     unsigned long long w[2] = {0, 0};
-    int it = 0;
     PGCP_CUDA(cudaMemcpyAsync(w, D.work.p, sizeof(w), cudaMemcpyDeviceToHost, s));
-    PGCP_CUDA(cudaMemcpyAsync(&it, D.out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     PGCP_CUDA(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    PGCP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
-    P.stats.pcg_ms += ms;
     // Per free row and iteration, with vector pairs of 2T bytes (T = 8 for
     // double-float, 4 for FP32): phase B row pointer 4, r 2T, p r/w 4T,
     // q r/w 4T; phase A diagonal 4, x r/w 4T, r r/w 4T, p 2T, q 2T
     // -> 8 + 22T.  Per stored entry: column 4 + value T (gathered r hits cache).
     const double T = D.f32 ? 4.0 : 8.0;
     P.stats.pcg_bytes += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
-    P.stats.pcg_launches += 1;
     return it;
 }
 

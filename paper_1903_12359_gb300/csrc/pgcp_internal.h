@@ -246,6 +246,8 @@ struct DfSystem {
     int64_t n = 0, nnz = 0;
     int dncp = 0, f32 = 0, grid = 0, per_sm = 0, minb = 4;
     int32_t nruns = 0;
+    int64_t runs_cap = 0;      // capacity of runs (rebuilt runs of a chunked solve fit)
+    int64_t covered = 0;       // rows the current runs cover
     DBuf<int32_t> rp, col;
     DBuf<unsigned char> val;   // nnz scalars (float2 or float)
     DBuf<double> sc;           // 1 / sqrt(diag), 0 at fixed rows

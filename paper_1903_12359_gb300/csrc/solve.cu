@@ -47,10 +47,19 @@ __global__ void k_translate(int64_t n, const int32_t* __restrict__ row_piece, co
     out[i] = v;
 }
 
-__global__ void k_final_init(int64_t n, const uint8_t* __restrict__ is_bnd, const double2* __restrict__ welded,
-                             int cold, double2* __restrict__ x) {
+// Start of the final solve: welded boundary values, interior from the weld map
+// (or 0 for a cold start).  Pieces of meshes dropped from a batch by the
+// welding get 0 everywhere: right-hand side 0, converged at once, and their
+// output is NaN after the gather.
+__global__ void k_final_init(int64_t n, const uint8_t* __restrict__ is_bnd, const int32_t* __restrict__ row_piece,
+                             const uint8_t* __restrict__ wchart, const double2* __restrict__ welded, int cold,
+                             double2* __restrict__ x) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (wchart[row_piece[i]] == 2) {
+        x[i] = make_double2(0.0, 0.0);
+        return;
+    }
     x[i] = (is_bnd[i] || !cold) ? welded[i] : make_double2(0.0, 0.0);
 }
 
@@ -139,8 +148,8 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     cudaStream_t s = ctx->stream;
     const int64_t n = P.Nc;
     P.final.alloc(n, s);
-    { k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.welded.p, ctx->opt.warm_start == PGCP_WARM_COLD,
-                                         P.final.p); ::pgcp::note_launch(); }
+    { k_final_init<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, P.row_piece.p, P.d_wchart.p, P.welded.p,
+                                         ctx->opt.warm_start == PGCP_WARM_COLD, P.final.p); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     P.stats.learned_pieces = 0;
     if (ctx->opt.warm_start == PGCP_WARM_LEARNED) P.stats.learned_pieces = learned_start(ctx, P, P.final.p);
