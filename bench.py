@@ -10,6 +10,11 @@ library's stream, barrier + synchronize on both sides, max over ranks; L2 is
 flushed with a 256 MB write before every step).  e2e repeats the measurement
 through the one-shot C call with host buffers (copies inside the timed region).
 
+On one GPU the line also carries "batched": the same path over the 256-mesh
+uneven batch (15M vertices, about 5,000 pieces of very different sizes) in one
+partition_batch call per step, with its own throughput, stages and the DNCP
+PCG's achieved bandwidth (--no-batch skips it).
+
 Under torchrun each rank runs its own mesh (different seed): independent
 problems, no collective on the data path, weak scaling.
 
@@ -49,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cold", action="store_true", help="skip the cold-start comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-mesh uneven batch (one GPU only)")
+    ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--local-precision", type=int, default=2,
                     help="DNCP solve: 0 FP64 PCG, 2 double-float PCG in FP64 refinement")
     return ap.parse_args()
@@ -82,6 +89,63 @@ def oracle_sample(n: int, seed: int) -> dict:
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- uneven batch
+
+BATCH_WORKLOAD = ("{n} height-field disks of the same recipe, vertex counts log-uniform in 5k-200k, each cut by "
+                  "a random grid into 4-32 pieces of uneven size; all meshes in one partition_batch call; disk maps")
+
+
+def _uneven_mesh(params):
+    from paper_1903_12359_gb300 import meshgen
+    return meshgen.uneven_mesh(params)
+
+
+def uneven_meshes(n_mesh: int):
+    """The uneven batch, meshed by a pool of spawned processes (no GPU state)."""
+    import multiprocessing as mp
+    from paper_1903_12359_gb300 import meshgen
+    params = meshgen.uneven_batch_params(n_mesh=n_mesh, seed=0)
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_uneven_mesh, params, chunksize=4)
+
+
+def run_batch(api, torch, ms, steps: int, warmup: int) -> dict:
+    """Throughput of the whole uneven batch in one call per step (inputs
+    resident in device memory, 15M vertices, larger than L2)."""
+    dev = [(torch.as_tensor(m.V, device="cuda"), torch.as_tensor(m.F, device="cuda", dtype=torch.int32),
+            torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)) for m in ms]
+    nv = sum(m.nv for m in ms)
+    ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, local_precision=api.DF64_REFINED)
+    rows = []
+    for i in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        part = ctx.partition_batch(dev)
+        part.local_param()
+        st_local = part.get_stats()
+        part.weld()
+        part.global_solve()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        st = dict(part.stats)
+        status = part.mesh_status()
+        part.free()
+        if i >= warmup:
+            rows.append((e0.elapsed_time(e1), st, st_local, status))
+    ms_step = sum(r[0] for r in rows) / len(rows)
+    st, st_local, status = rows[-1][1], rows[-1][2], rows[-1][3]
+    gbs = sum(r[2]["pcg_bytes"] for r in rows) / (sum(r[2]["pcg_ms"] for r in rows) / 1000.0) / 1e9
+    return {"workload": BATCH_WORKLOAD.format(n=len(ms)), "meshes": len(ms), "nv": nv, "pieces": st["K"],
+            "value": nv / (ms_step / 1000.0), "unit": "vertices/s", "ms_per_step": ms_step, "steps": len(rows),
+            "dropped_meshes": sum(1 for c in status if c != "OK"),
+            "stages_ms": {k: st[k] for k in ("ms_partition", "ms_assembly", "ms_local", "ms_weld", "ms_final")},
+            "iterations": {"dncp": st["dncp_iters"], "final": st["final_iters"]},
+            "residual": {"dncp": st["dncp_relres"], "final": st["final_relres"]},
+            "dncp_pcg": {"achieved_gbs": gbs, "launches": st_local["pcg_launches"]}}
 
 
 # ---------------------------------------------------------------- clocks
@@ -202,6 +266,9 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle runs in its own process, started before any GPU work here
         cpu = oracle_sample(SAMPLE_N, args.seed)
+    batch_meshes = None
+    if ws == 1 and not args.no_batch:
+        batch_meshes = uneven_meshes(args.batch_meshes)   # after the oracle sample: no competing cores
     import numpy as np
     import torch
     torch.cuda.set_device(local)
@@ -304,6 +371,9 @@ def main():
         e2e = {"value": ws * m.nv * args.steps / (ems / 1000.0), "unit": "vertices/s",
                "h2d_bytes_per_step": int(Vh.nbytes + Fh.nbytes + Lh.nbytes),
                "d2h_bytes_per_step": int(m.nv * 2 * 8), "wall_s": wall}
+    batched = None
+    if batch_meshes is not None:
+        batched = run_batch(api, torch, batch_meshes, steps=2, warmup=1)
     if rank != 0:
         return 0
     peaks = measured_peaks()
@@ -347,6 +417,9 @@ def main():
                            "final_learned": stats_learned[-1]["final_iters"]},
             "residual": {"dncp": s0["dncp_relres"], "final": s0["final_relres"]},
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+    if batched is not None:
+        batched["dncp_pcg"]["frac"] = batched["dncp_pcg"]["achieved_gbs"] / peak
+        line["batched"] = batched
     if cpu:
         line["cpu_baseline"] = {"value": cpu["nv"] / cpu["seconds"], "unit": "vertices/s", "cores": 1,
                                 "kind": "oracle",

@@ -478,12 +478,13 @@ def icosphere_sh_mesh(subdiv: int = 8, seed: int = 0, lmax: int = 6, amp: float 
     return Mesh(U, F, labels, "closed", f"icosphere_sd{subdiv}_s{seed}")
 
 
-def uneven_batch(n_mesh: int = 256, seed: int = 0, nmin: int = 5000, nmax: int = 200000,
-                 kmin: int = 4, kmax: int = 32) -> list:
-    """Many height-field disks, log-uniform sizes, 4..32 pieces of uneven size.
+def uneven_batch_params(n_mesh: int = 256, seed: int = 0, nmin: int = 5000, nmax: int = 200000,
+                        kmin: int = 4, kmax: int = 32) -> list:
+    """(N, nx, ny, mesh seed) of each mesh of ``uneven_batch``, without meshing.
 
-    Each mesh draws K ~ U{kmin..kmax} and is cut by an nx x ny grid of straight
-    lines at random positions (nx * ny >= K, cells outside the disk vanish).
+    Each mesh draws N log-uniform in [nmin, nmax] and K ~ U{kmin..kmax}, and is
+    cut by an nx x ny grid (nx = ceil(sqrt K), ny = ceil(K / nx)) of straight
+    lines at random positions (cells outside the disk vanish).
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -492,8 +493,20 @@ def uneven_batch(n_mesh: int = 256, seed: int = 0, nmin: int = 5000, nmax: int =
         K = int(rng.integers(kmin, kmax + 1))
         nx = int(math.ceil(math.sqrt(K)))
         ny = int(math.ceil(K / nx))
-        out.append(heightfield_disk_mesh(N, seed=seed * 100003 + i, nx=nx, ny=ny, uneven=True))
+        out.append((N, nx, ny, seed * 100003 + i))
     return out
+
+
+def uneven_mesh(params) -> Mesh:
+    """One mesh of ``uneven_batch`` from its ``uneven_batch_params`` entry."""
+    N, nx, ny, s = params
+    return heightfield_disk_mesh(N, seed=s, nx=nx, ny=ny, uneven=True)
+
+
+def uneven_batch(n_mesh: int = 256, seed: int = 0, nmin: int = 5000, nmax: int = 200000,
+                 kmin: int = 4, kmax: int = 32) -> list:
+    """Many height-field disks, log-uniform sizes, 4..32 pieces of uneven size."""
+    return [uneven_mesh(p) for p in uneven_batch_params(n_mesh, seed, nmin, nmax, kmin, kmax)]
 
 
 def he_normal(seed: int, shapes) -> np.ndarray:
