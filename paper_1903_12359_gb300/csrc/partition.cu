@@ -407,45 +407,63 @@ void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels, const int3
         PGCP_CUDA(cudaMemcpyAsync(h_piece.data(), hpiece.p, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     }
     PGCP_CUDA(cudaStreamSynchronize(s));
-    // ---- loops (host): per piece, next[] over boundary rows, walk from the smallest global id
-    std::vector<std::vector<std::pair<int4, int>>> per(K);
-    for (size_t i = 0; i < nh; ++i) per[h_piece[i]].push_back({h_he[i], 0});
+    // ---- loops (host): per piece, the half-edge leaving each boundary row (a
+    // dense table over the piece's rows), walked from the smallest global id
+    std::vector<int64_t> hoff(K + 1, 0);
+    for (size_t i = 0; i < nh; ++i) ++hoff[h_piece[i] + 1];
+    for (int64_t i = 0; i < K; ++i) hoff[i + 1] += hoff[i];
+    std::vector<int4> hs(nh);
+    {
+        std::vector<int64_t> fill(hoff.begin(), hoff.end() - 1);
+        for (size_t i = 0; i < nh; ++i) hs[fill[h_piece[i]]++] = h_he[i];
+    }
+    int64_t maxrows = 1;
+    for (int64_t i = 0; i < K; ++i) maxrows = std::max<int64_t>(maxrows, P.voff[i + 1] - P.voff[i]);
+    std::vector<int32_t> out_of(maxrows, -1);   // half-edge leaving a row (index into the piece's list)
     P.loff.assign(K + 1, 0);
     P.loop_rows.clear();
     P.loop_glob.clear();
     for (int64_t i = 0; i < K; ++i) {
-        auto& e = per[i];
-        if (e.empty()) fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " has no boundary (not a disk)");
-        std::sort(e.begin(), e.end(), [](const std::pair<int4, int>& a, const std::pair<int4, int>& b) {
-            return a.first.x < b.first.x;
-        });
-        for (size_t t = 1; t < e.size(); ++t)
-            if (e[t].first.x == e[t - 1].first.x)
-                fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " is pinched at vertex " +
-                                          std::to_string(e[t].first.z));
-        // index by row
+        const int4* e = hs.data() + hoff[i];
+        const int64_t ne = hoff[i + 1] - hoff[i];
+        const int64_t r0 = P.voff[i];
+        if (ne == 0) fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " has no boundary (not a disk)");
+        for (int64_t t = 0; t < ne; ++t) {
+            if (e[t].x < r0 || e[t].x >= P.voff[i + 1]) {
+                for (int64_t u = 0; u < t; ++u) out_of[e[u].x - r0] = -1;
+                fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + ": boundary half-edge outside the piece");
+            }
+            int32_t& slot = out_of[e[t].x - r0];
+            if (slot >= 0) {
+                for (int64_t u = 0; u < t; ++u) out_of[e[u].x - r0] = -1;
+                fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " is pinched at vertex " + std::to_string(e[t].z));
+            }
+            slot = (int32_t)t;
+        }
         auto find = [&](int row) -> int {
-            auto it = std::lower_bound(e.begin(), e.end(), row,
-                                       [](const std::pair<int4, int>& a, int r) { return a.first.x < r; });
-            if (it == e.end() || it->first.x != row) return -1;
-            return (int)(it - e.begin());
+            if (row < r0 || row >= P.voff[i + 1]) return -1;
+            return out_of[row - r0];
         };
         int start = 0;
-        for (size_t t = 1; t < e.size(); ++t)
-            if (e[t].first.z < e[start].first.z) start = (int)t;
+        for (int64_t t = 1; t < ne; ++t)
+            if (e[t].z < e[start].z) start = (int)t;
         int cur = start;
         size_t len = 0;
+        bool broken = false;
         do {
-            P.loop_rows.push_back(e[cur].first.x);
-            P.loop_glob.push_back(e[cur].first.z);
-            e[cur].second = 1;
+            P.loop_rows.push_back(e[cur].x);
+            P.loop_glob.push_back(e[cur].z);
             ++len;
-            int nx = find(e[cur].first.y);
-            if (nx < 0 || len > e.size())
-                fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + ": broken boundary loop");
+            int nx = find(e[cur].y);
+            if (nx < 0 || (int64_t)len > ne) {
+                broken = true;
+                break;
+            }
             cur = nx;
         } while (cur != start);
-        if (len != e.size()) fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " has more than one boundary loop");
+        for (int64_t t = 0; t < ne; ++t) out_of[e[t].x - r0] = -1;
+        if (broken) fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + ": broken boundary loop");
+        if ((int64_t)len != ne) fail(PGCP_E_TOPOLOGY, "piece " + std::to_string(i) + " has more than one boundary loop");
         int64_t nvi = P.voff[i + 1] - P.voff[i], nfi = P.foff[i + 1] - P.foff[i];
         int64_t E = (3 * nfi + (int64_t)len) / 2;
         if ((3 * nfi + (int64_t)len) % 2 != 0 || nvi - E + nfi != 1)

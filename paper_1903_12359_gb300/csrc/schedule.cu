@@ -18,8 +18,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 #include "pgcp_internal.h"
@@ -63,17 +61,20 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
     P.pin0.assign(K, 0);
     P.pin1.assign(K, 0);
     P.ref.assign(K, -1);
-    for (int32_t i = 0; i < K; ++i) {
-        int64_t b = P.loff[i + 1] - P.loff[i];
-        P.pin0[i] = P.loop_rows[P.loff[i]];
-        P.pin1[i] = P.loop_rows[P.loff[i] + b / 2];
-        int64_t n = P.voff[i + 1] - P.voff[i];
-        std::unordered_set<int64_t> bnd(P.loop_rows.begin() + P.loff[i], P.loop_rows.begin() + P.loff[i + 1]);
-        for (int64_t t = 0; t < n; ++t) {
-            int64_t r = P.voff[i] + (n / 2 + t) % n;
-            if (!bnd.count(r)) {
-                P.ref[i] = r;
-                break;
+    {
+        std::vector<char> bnd(P.Nc, 0);   // boundary rows
+        for (int64_t r : P.loop_rows) bnd[r] = 1;
+        for (int32_t i = 0; i < K; ++i) {
+            int64_t b = P.loff[i + 1] - P.loff[i];
+            P.pin0[i] = P.loop_rows[P.loff[i]];
+            P.pin1[i] = P.loop_rows[P.loff[i] + b / 2];
+            int64_t n = P.voff[i + 1] - P.voff[i];
+            for (int64_t t = 0; t < n; ++t) {
+                int64_t r = P.voff[i] + (n / 2 + t) % n;
+                if (!bnd[r]) {
+                    P.ref[i] = r;
+                    break;
+                }
             }
         }
     }
@@ -107,14 +108,34 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
         std::vector<int32_t> loop;
         int32_t single;
     };
+    // Dense per-mesh tables over the mesh's vertex range [base, base + nv),
+    // reused from mesh to mesh and cleared by epoch stamps instead of hashing:
+    //   cp_off / cp: (piece, row) of every loop copy of a vertex, pieces ascending;
+    //   st_b / nx_b: B's loop vertices and their successors (directed edges of B);
+    //   st_a, st_arc: A's loop vertices, the shared arc's vertices.
+    int64_t maxnv = 1;
+    for (const MeshInfo& M : P.meshes) maxnv = std::max<int64_t>(maxnv, M.nv);
+    std::vector<int64_t> cp_off(maxnv + 1);
+    std::vector<std::pair<int32_t, int64_t>> cp;
+    std::vector<int32_t> st_b(maxnv, 0), nx_b(maxnv, 0), st_a(maxnv, 0), st_arc(maxnv, 0), mark(K, 0);
+    int32_t epoch = 0;
+    int64_t base = 0;
     // copy row of each loop vertex in the lowest-label piece of `pieces` holding it
     auto rows_of = [&](const std::vector<int32_t>& pieces, const std::vector<int32_t>& ids) {
-        std::unordered_map<int32_t, int64_t> row;
-        for (int32_t pc : pieces)
-            for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) row.emplace(P.loop_glob[t], P.loop_rows[t]);
+        ++epoch;
+        for (int32_t pc : pieces) mark[pc] = epoch;
         std::vector<int64_t> out;
         out.reserve(ids.size());
-        for (int32_t g : ids) out.push_back(row.at(g));
+        for (int32_t g : ids) {
+            int64_t r = -1;
+            for (int64_t c = cp_off[g - base]; c < cp_off[g - base + 1]; ++c)
+                if (mark[cp[c].first] == epoch) {
+                    r = cp[c].second;
+                    break;
+                }
+            if (r < 0) fail(PGCP_E_SCHEDULE, "welding sequence vertex " + std::to_string(g) + " is on no member loop");
+            out.push_back(r);
+        }
         return out;
     };
     // the weld of B onto A, if their loops share one contiguous arc (or, for the
@@ -122,13 +143,17 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
     auto pair_weld = [&](const Comp& A, const Comp& B, bool closed_final, WeldPlan& W) -> bool {
         const std::vector<int32_t>& A_loop = A.loop;
         const std::vector<int32_t>& B_loop = B.loop;
-        std::unordered_set<uint64_t> b_edges;
-        for (size_t t = 0; t < B_loop.size(); ++t) b_edges.insert(dkey(B_loop[t], B_loop[(t + 1) % B_loop.size()]));
+        ++epoch;
+        for (size_t t = 0; t < B_loop.size(); ++t) {   // directed edges of B: g -> nx_b[g]
+            st_b[B_loop[t] - base] = epoch;
+            nx_b[B_loop[t] - base] = B_loop[(t + 1) % B_loop.size()];
+        }
+        auto b_edge = [&](int32_t u, int32_t v) { return st_b[u - base] == epoch && nx_b[u - base] == v; };
         const size_t m1 = A_loop.size();
         std::vector<char> shared(m1);
         bool any = false, all = true;
         for (size_t t = 0; t < m1; ++t) {
-            shared[t] = b_edges.count(dkey(A_loop[(t + 1) % m1], A_loop[t])) ? 1 : 0;
+            shared[t] = b_edge(A_loop[(t + 1) % m1], A_loop[t]) ? 1 : 0;
             any |= shared[t];
             all &= shared[t] != 0;
         }
@@ -162,10 +187,10 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
         if (k < 2) return false;
         std::vector<int32_t> a(A_loop.begin() + i0, A_loop.end());
         a.insert(a.end(), A_loop.begin(), A_loop.begin() + i0);
-        std::unordered_set<int32_t> arcv(a.begin(), a.begin() + k + 1);
-        std::unordered_set<int32_t> aset(A_loop.begin(), A_loop.end());
-        for (int32_t g : B_loop)
-            if (aset.count(g) && !arcv.count(g)) return false;
+        for (int32_t g : A_loop) st_a[g - base] = epoch;
+        for (int32_t t = 0; t <= k; ++t) st_arc[a[t] - base] = epoch;
+        for (int32_t g : B_loop)   // B touches A only along the arc
+            if (st_a[g - base] == epoch && st_arc[g - base] != epoch) return false;
         size_t j = std::find(rb.begin(), rb.end(), a[0]) - rb.begin();
         std::vector<int32_t> b(rb.begin() + j, rb.end());
         b.insert(b.end(), rb.begin(), rb.begin() + j);
@@ -186,17 +211,55 @@ void build_schedule(pgcp_ctx* ctx, Part& P) {
             if (P.closed) fail(PGCP_E_TOPOLOGY, "a closed surface needs at least two pieces");
             continue;
         }
+        base = M.v0;
+        std::fill(cp_off.begin(), cp_off.begin() + M.nv + 1, 0);
+        for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece; ++pc)
+            for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) ++cp_off[P.loop_glob[t] - base + 1];
+        for (int64_t v = 0; v < M.nv; ++v) cp_off[v + 1] += cp_off[v];
+        cp.resize(cp_off[M.nv]);
+        {
+            std::vector<int64_t> fill(cp_off.begin(), cp_off.begin() + M.nv);
+            for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece; ++pc)   // pieces ascending
+                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t)
+                    cp[fill[P.loop_glob[t] - base]++] = {pc, P.loop_rows[t]};
+        }
         std::vector<Comp> comps;
         for (int32_t i = M.piece0; i < M.piece0 + M.npiece; ++i) comps.push_back(Comp{{i}, loop_of(i), 1});
         int32_t level = 0;
         while (comps.size() > 1) {
             const bool final2 = P.closed && comps.size() == 2;
+            // Components that share a loop edge (pair_weld fails for all others,
+            // so scanning only these keeps the pairing order): every loop edge,
+            // undirected, with its component, sorted by edge.
+            std::vector<std::pair<uint64_t, int32_t>> ec;
+            for (size_t c = 0; c < comps.size(); ++c) {
+                const std::vector<int32_t>& L = comps[c].loop;
+                for (size_t t = 0; t < L.size(); ++t) {
+                    const int32_t u = L[t], v = L[(t + 1) % L.size()];
+                    ec.emplace_back(dkey(std::min(u, v), std::max(u, v)), (int32_t)c);
+                }
+            }
+            std::sort(ec.begin(), ec.end());
+            std::vector<std::vector<int32_t>> nbr(comps.size());
+            for (size_t a = 0; a < ec.size();) {
+                size_t b = a + 1;
+                while (b < ec.size() && ec[b].first == ec[a].first) ++b;
+                for (size_t x = a; x < b; ++x)
+                    for (size_t y = a; y < b; ++y)
+                        if (ec[x].second != ec[y].second) nbr[ec[x].second].push_back(ec[y].second);
+                a = b;
+            }
+            for (auto& v : nbr) {
+                std::sort(v.begin(), v.end());
+                v.erase(std::unique(v.begin(), v.end()), v.end());
+            }
             std::vector<char> used(comps.size(), 0);
             std::vector<Comp> next;
             for (size_t i = 0; i < comps.size(); ++i) {
                 if (used[i]) continue;
-                for (size_t j = i + 1; j < comps.size(); ++j) {
-                    if (used[j]) continue;
+                for (int32_t jj : nbr[i]) {
+                    const size_t j = (size_t)jj;
+                    if (j <= i || used[j]) continue;
                     WeldPlan W;
                     if (!pair_weld(comps[i], comps[j], final2, W)) continue;
                     W.mesh = (int32_t)mi;
