@@ -51,7 +51,10 @@ class Result:
     seam_mismatch: float = 0.0
 
 
-def _weld_once(res: Result, wd, map_interior: bool, sphere_close: bool):
+def _weld_phase1(res: Result, wd, sphere_close: bool):
+    """Algorithms 1-2 on the weld's sequence points (read from the current
+    boundary coordinates of its pieces): the two chains and the final images
+    of the arc points on each side."""
     P = res.part
     k = wd.k
     members = wd.members
@@ -101,9 +104,20 @@ def _weld_once(res: Result, wd, map_interior: bool, sphere_close: bool):
     chainA = gA + hs + [TA]
     chainB = gB + hs + [TB]
     res.weld_chains.append((chainA, chainB))
+    return chainA, chainB, arc_A, arc_B
+
+
+def _weld_phase2(res: Result, wd, ph1, map_interior: bool, pieces=None):
+    """The weld's chains applied to the points of its pieces (all, or those
+    in ``pieces``); the arc points take their phase-1 images."""
+    P = res.part
+    k = wd.k
+    chainA, chainB, arc_A, arc_B = ph1
     arc_pos = {g: j for j, g in enumerate(wd.a[:k + 1].tolist())}
     # apply to every point of every involved piece
-    for pc, chain, arc in [(pc, chainA, arc_A) for pc in members] + [(pc, chainB, arc_B) for pc in b_members]:
+    for pc, chain, arc in [(pc, chainA, arc_A) for pc in wd.members] + [(pc, chainB, arc_B) for pc in wd.b_members]:
+        if pieces is not None and pc not in pieces:
+            continue
         g_ids = P.verts[pc]
         on_loop = np.zeros(g_ids.size, dtype=bool)
         gl = {g: li for li, g in enumerate(g_ids.tolist())}
@@ -127,10 +141,16 @@ def _weld_once(res: Result, wd, map_interior: bool, sphere_close: bool):
             zi[~on_loop] = np.nan
         res.welded[pc] = zr + 1j * zi
         res.welded_inf[pc] = zinf
+
+
+def _weld_once(res: Result, wd, map_interior: bool, sphere_close: bool):
+    _weld_phase2(res, wd, _weld_phase1(res, wd, sphere_close), map_interior)
     return res
 
 
-def _disk_step(res: Result, map_interior: bool):
+def _disk_phase1(res: Result):
+    """The geodesic algorithm on the global boundary loop: its chain and the
+    images of the loop points."""
     P = res.part
     # global boundary loop = C's loop after all welds (or the single piece's loop)
     C_loop = res.welds[-1].new_loop if res.welds else P.loops[0]
@@ -145,8 +165,18 @@ def _disk_step(res: Result, map_interior: bool):
     cref = -1.0 if res.welds else 0.0
     chain, img = W.geodesic_disk(W.Pts(zr, zi), W.Pts([cref], [0.0]))
     res.disk_chain = chain
+    return chain, img, C_loop
+
+
+def _disk_phase2(res: Result, ph1, map_interior: bool, pieces=None):
+    """The disk chain applied to the points of the pieces (all, or those in
+    ``pieces``); the global boundary points take their phase-1 images."""
+    P = res.part
+    chain, img, C_loop = ph1
     bpos = {g: j for j, g in enumerate(C_loop.tolist())}
     for pc in range(P.K):
+        if pieces is not None and pc not in pieces:
+            continue
         g_ids = P.verts[pc]
         gl = {g: li for li, g in enumerate(g_ids.tolist())}
         on_loop = np.zeros(g_ids.size, dtype=bool)
@@ -163,6 +193,10 @@ def _disk_step(res: Result, map_interior: bool):
             j = bpos[int(g_ids[li])]
             z[li] = complex(img.re[j], img.im[j])
         res.welded[pc] = z
+
+
+def _disk_step(res: Result, map_interior: bool):
+    _disk_phase2(res, _disk_phase1(res), map_interior)
 
 
 def harmonic_solve(L, loop_local: np.ndarray, ub: np.ndarray) -> np.ndarray:
