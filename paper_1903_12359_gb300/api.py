@@ -63,6 +63,17 @@ class Distortion(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AreaResult(C.Structure):
+    _fields_ = [("param_re", C.c_double), ("param_im", C.c_double), ("before", C.c_double), ("after", C.c_double),
+                ("evals", C.c_int32), ("status", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["param"] = complex(self.param_re, self.param_im)
+        d["status"] = STATUS.get(self.status, str(self.status))
+        return d
+
+
 # exported symbols and their signatures (name -> (restype, argtypes))
 _P = C.c_void_p
 SIGNATURES = {
@@ -89,6 +100,8 @@ SIGNATURES = {
     "pgcp_global_solve": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(Stats)]),
     "pgcp_metrics": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
     "pgcp_metrics_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
+    "pgcp_area_distortion": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double)]),
+    "pgcp_area_mobius": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(AreaResult)]),
     "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
                            C.POINTER(Stats)]),
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
@@ -383,6 +396,23 @@ class Part:
         m = Distortion()
         self.ctx.check(load().pgcp_metrics(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
         return m.as_dict()
+
+    def area_distortion(self, U):
+        """pgcp_area_distortion: mean |d_area| (Section 6.2) of each mesh's planar map U."""
+        n = self.info()["n_mesh"]
+        out = (C.c_double * n)()
+        self.ctx.check(load().pgcp_area_distortion(self.ctx.h, self.h, _ptr(U.contiguous()), out))
+        return list(out)
+
+    def area_mobius(self, U, variant):
+        """pgcp_area_mobius: the Mobius area step (Section 6.2) on U in place
+        (a contiguous float64 CUDA tensor); one result dict per mesh."""
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.is_contiguous() and U.dtype == torch.float64):
+            raise ValueError("U must be a contiguous float64 CUDA tensor (updated in place)")
+        n = self.info()["n_mesh"]
+        out = (AreaResult * n)()
+        self.ctx.check(load().pgcp_area_mobius(self.ctx.h, self.h, _ptr(U), int(variant), out))
+        return [r.as_dict() for r in out]
 
     def metrics_noalloc(self, U):
         """pgcp_metrics_noalloc: the same statistics with no device allocation,

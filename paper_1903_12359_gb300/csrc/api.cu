@@ -397,6 +397,20 @@ pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, 
     });
 }
 
+pgcp_status pgcp_area_distortion(pgcp_ctx* ctx, const pgcp_part* part, const double* U, double* mean_abs) {
+    return guard(ctx, [&] {
+        if (!part || !U || !mean_abs) fail(PGCP_E_ARG, "null argument");
+        area_distortion(ctx, part->p, U, mean_abs);
+    });
+}
+
+pgcp_status pgcp_area_mobius(pgcp_ctx* ctx, const pgcp_part* part, double* U, int32_t variant, pgcp_area_result* out) {
+    return guard(ctx, [&] {
+        if (!part || !U || !out) fail(PGCP_E_ARG, "null argument");
+        area_mobius(ctx, part->p, U, variant, out);
+    });
+}
+
 pgcp_status pgcp_metrics_noalloc(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met) {
     return guard(ctx, [&] {
         if (!ctx || !part || !U || !met) fail(PGCP_E_ARG, "null argument");

@@ -288,6 +288,9 @@ void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distort
 // Same statistics on a fixed device-side scratch array; no allocation.
 void compute_metrics_noalloc(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
 int64_t metrics_noalloc_max_faces();
+// Area distortion and the Mobius area step (Section 6.2), one result per mesh.
+void area_distortion(pgcp_ctx* ctx, const Part& P, const double* U, double* mean_abs);
+void area_mobius(pgcp_ctx* ctx, const Part& P, double* U, int variant, pgcp_area_result* out);
 
 // BF16 tensor-core GEMM (gemm_tc.cu): C = epi(A . Bt^T), A [M x K], Bt [N x K],
 // both bf16 with K contiguous.  epi 0: store FP32; 1: + bias, ReLU, store bf16

@@ -52,7 +52,7 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"pgcp_options": api.Options, "pgcp_stats": api.Stats, "pgcp_distortion": api.Distortion,
-               "pgcp_mesh_desc": api.MeshDesc}
+               "pgcp_mesh_desc": api.MeshDesc, "pgcp_area_result": api.AreaResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pgcp.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
