@@ -375,6 +375,20 @@ def main():
         e2e = {"value": ws * m.nv * args.steps / (ems / 1000.0), "unit": "vertices/s",
                "h2d_bytes_per_step": int(Vh.nbytes + Fh.nbytes + Lh.nbytes),
                "d2h_bytes_per_step": int(m.nv * 2 * 8), "wall_s": wall}
+    # the Mobius area step (Section 6.2) on the last output, once (not in the timed steps)
+    area = None
+    if rank == 0:
+        part_a = ctx.partition(Vd, Fd, face_labels=Ld)
+        U_a = out.clone()
+        ea0 = torch.cuda.Event(enable_timing=True)
+        ea1 = torch.cuda.Event(enable_timing=True)
+        ea0.record(ctx.stream)
+        ra = part_a.area_mobius(U_a, api.DISK)[0]
+        ea1.record(ctx.stream)
+        torch.cuda.synchronize()
+        area = {"ms": ea0.elapsed_time(ea1), "evals": ra["evals"], "mean_abs_d_area_before": ra["before"],
+                "mean_abs_d_area_after": ra["after"], "alpha": [ra["param_re"], ra["param_im"]]}
+        part_a.free()
     batched = None
     if batch_meshes is not None:
         batched = run_batch(api, torch, batch_meshes, steps=2, warmup=1)
@@ -427,6 +441,8 @@ def main():
                            "final_learned": stats_learned[-1]["final_iters"]},
             "residual": {"dncp": s0["dncp_relres"], "final": s0["final_relres"]},
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+    if area is not None:
+        line["area_step"] = area
     if batched is not None:
         batched["dncp_pcg"]["frac"] = batched["dncp_pcg"]["achieved_gbs"] / peak
         if batched["final_pcg"]["achieved_gbs"] is not None:
