@@ -14,11 +14,18 @@ minimises mean |d_area| of f o phi, over the families Section 6.2 names:
   (q = 0: the identity coset; otherwise the pole 1/q), and f_q o f_p = f_{p+q}.
   The step searches q.  (Reading: the paper optimises all eight real
   parameters; the other six only move the result by a similarity.)
+* sphere: tau^-1 o f o tau for a Mobius map f, i.e. a conformal map of the
+  sphere; rotations leave chordal areas unchanged, and every such map is a
+  rotation after exactly one ball automorphism (Ahlfors' form)
+      T_a(x) = ((1 - |a|^2)(x - a) - |x - a|^2 a) / (1 - 2<a, x> + |a|^2 |x|^2),  |a| < 1,
+  which keeps the unit sphere (T_0 = id, T_a(a) = 0, T_a(0) = -a).  The step
+  searches a in R^3.  Parameter areas on the sphere are those of the chordal
+  triangles (the reading of the angle metric), which must face outwards.
 The search is Nelder and Mead's simplex method (Computer Journal 7, 1965) on
-the two real parameters, from the identity, with reflection 1, expansion 2,
+the real parameters, from the identity, with reflection 1, expansion 2,
 contraction 1/2 and shrink 1/2; a parameter that leaves the family's domain
-(|alpha| >= 1) or gives any face a non-positive area (the pole of f inside the
-image) scores +inf.
+(|alpha| >= 1, |a| >= 1) or gives any face a non-positive area (the pole of f
+inside the image) scores +inf.
 """
 from __future__ import annotations
 
@@ -57,6 +64,46 @@ def mobius(variant: str, p: complex, z: np.ndarray) -> np.ndarray:
     raise ValueError(variant)
 
 
+def ball_automorphism(a: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """T_a on the rows of X (points of R^3)."""
+    a = np.asarray(a, dtype=np.float64)
+    aa = float(a @ a)
+    xa = X @ a
+    xx = (X * X).sum(axis=1)
+    d = X - a
+    dd = (d * d).sum(axis=1)
+    num = (1.0 - aa) * d - dd[:, None] * a
+    return num / (1.0 - 2.0 * xa + aa * xx)[:, None]
+
+
+def chordal_areas(X: np.ndarray, F: np.ndarray) -> np.ndarray:
+    """Area of each chordal triangle, negative when it faces inwards."""
+    a, b, c = X[F[:, 0]], X[F[:, 1]], X[F[:, 2]]
+    cr = np.cross(b - a, c - a)
+    ar = 0.5 * np.sqrt((cr * cr).sum(axis=1))
+    return np.where((cr * (a + b + c)).sum(axis=1) > 0.0, ar, -ar)
+
+
+def sphere_area_distortion(V: np.ndarray, F: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """d_area per face of a spherical map X (chordal parameter triangles)."""
+    at = surface_areas(V, F)
+    af = chordal_areas(X, F)
+    return np.log((af / af.sum()) / (at / at.sum()))
+
+
+def sphere_objective(V, F, X, a) -> float:
+    """mean |d_area| of T_a o X; +inf for |a| >= 1 or an inward-facing triangle."""
+    a = np.asarray(a, dtype=np.float64)
+    if float(a @ a) >= 1.0:
+        return np.inf
+    af = chordal_areas(ball_automorphism(a, X), F)
+    if not np.all(np.isfinite(af)) or np.any(af <= 0.0):
+        return np.inf
+    at = surface_areas(V, F)
+    d = np.log((af / af.sum()) / (at / at.sum()))
+    return float(np.abs(d).mean())
+
+
 def objective(V, F, U, variant: str, p: complex) -> float:
     """mean |d_area| of f_p o U; +inf outside the family's domain or on a fold."""
     if variant == "disk" and abs(p) >= 1.0:
@@ -72,42 +119,52 @@ def objective(V, F, U, variant: str, p: complex) -> float:
 
 
 def nelder_mead(fun, x0, step=NM_STEP, ftol=NM_FTOL, xtol=NM_XTOL, maxit=NM_MAXIT):
-    """Nelder-Mead on R^2: returns (best point, best value, evaluations)."""
-    pts = [np.array(x0, dtype=np.float64), np.array(x0) + [step, 0.0], np.array(x0) + [0.0, step]]
+    """Nelder-Mead on R^n: returns (best point, best value, evaluations)."""
+    x0 = np.array(x0, dtype=np.float64)
+    n = x0.size
+    pts = [x0.copy()]
+    for i in range(n):
+        e = x0.copy()
+        e[i] += step
+        pts.append(e)
     val = [fun(x) for x in pts]
-    evals = 3
+    evals = n + 1
+    w = n                                               # index of the worst after sorting
     for _ in range(maxit):
-        order = sorted(range(3), key=lambda i: val[i])
+        order = sorted(range(n + 1), key=lambda i: val[i])
         pts = [pts[i] for i in order]
         val = [val[i] for i in order]
-        size = max(np.abs(pts[i] - pts[0]).max() for i in (1, 2))
-        if np.isfinite(val[2]) and val[2] - val[0] <= ftol and size <= xtol:
+        size = max(np.abs(pts[i] - pts[0]).max() for i in range(1, n + 1))
+        if np.isfinite(val[w]) and val[w] - val[0] <= ftol and size <= xtol:
             break
-        c = 0.5 * (pts[0] + pts[1])                   # centroid of the two best
-        xr = c + (c - pts[2])                           # reflection
+        c = pts[0].copy()                               # centroid of the n best
+        for i in range(1, n):
+            c = c + pts[i]
+        c = c / n
+        xr = c + (c - pts[w])                           # reflection
         fr = fun(xr)
         evals += 1
         if fr < val[0]:
-            xe = c + 2.0 * (c - pts[2])                 # expansion
+            xe = c + 2.0 * (c - pts[w])                 # expansion
             fe = fun(xe)
             evals += 1
             if fe < fr:
-                pts[2], val[2] = xe, fe
+                pts[w], val[w] = xe, fe
             else:
-                pts[2], val[2] = xr, fr
-        elif fr < val[1]:
-            pts[2], val[2] = xr, fr
+                pts[w], val[w] = xr, fr
+        elif fr < val[w - 1]:
+            pts[w], val[w] = xr, fr
         else:
-            if fr < val[2]:                             # outside contraction
+            if fr < val[w]:                             # outside contraction
                 xc = c + 0.5 * (xr - c)
             else:                                       # inside contraction
-                xc = c + 0.5 * (pts[2] - c)
+                xc = c + 0.5 * (pts[w] - c)
             fc = fun(xc)
             evals += 1
-            if fc < min(fr, val[2]):
-                pts[2], val[2] = xc, fc
+            if fc < min(fr, val[w]):
+                pts[w], val[w] = xc, fc
             else:                                       # shrink towards the best
-                for i in (1, 2):
+                for i in range(1, n + 1):
                     pts[i] = pts[0] + 0.5 * (pts[i] - pts[0])
                     val[i] = fun(pts[i])
                     evals += 1
@@ -116,7 +173,12 @@ def nelder_mead(fun, x0, step=NM_STEP, ftol=NM_FTOL, xtol=NM_XTOL, maxit=NM_MAXI
 
 
 def area_step(V, F, U, variant: str):
-    """The Mobius area step: (parameter, mean |d_area| before, after, evaluations, mapped U)."""
+    """The Mobius area step: (parameter, mean |d_area| before, after, evaluations, mapped U).
+    For "sphere" U is [n, 3] on the unit sphere and the parameter is a in R^3."""
+    if variant == "sphere":
+        before = sphere_objective(V, F, U, np.zeros(3))
+        a, after, evals = nelder_mead(lambda x: sphere_objective(V, F, U, x), [0.0, 0.0, 0.0])
+        return a, before, after, evals, ball_automorphism(a, U)
     before = objective(V, F, U, variant, 0j)
     x, after, evals = nelder_mead(lambda x: objective(V, F, U, variant, complex(x[0], x[1])), [0.0, 0.0])
     p = complex(x[0], x[1])

@@ -94,3 +94,29 @@ def test_step_on_the_small_disk_case():
     assert abs(p) < 1.0 and after <= before
     assert abs(before - np.abs(AR.area_distortion(m.V, m.F, r.out)).mean()) < 1e-14
     assert np.abs(np.hypot(W[:, 0], W[:, 1]).max() - 1.0) < 1e-12   # still the unit disk
+
+
+def test_ball_automorphisms():
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(40, 3))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    a = np.array([0.3, -0.2, 0.45])
+    Y = AR.ball_automorphism(a, X)
+    assert np.abs(np.linalg.norm(Y, axis=1) - 1.0).max() < 1e-14          # keeps the sphere
+    assert np.abs(AR.ball_automorphism(np.zeros(3), X) - X).max() == 0.0   # T_0 = id
+    assert np.abs(AR.ball_automorphism(a, a[None, :])).max() < 1e-15      # T_a(a) = 0
+    assert np.abs(AR.ball_automorphism(a, np.zeros((1, 3))) + a).max() < 1e-15   # T_a(0) = -a
+    Z = AR.ball_automorphism(-a, Y)                 # T_{-a} o T_a fixes 0: a rotation
+    assert np.abs(Z @ Z.T - X @ X.T).max() < 1e-12
+
+
+def test_step_undoes_a_known_sphere_automorphism():
+    m = meshgen.icosphere_sh_mesh(subdiv=3, seed=0, amp=0.0)
+    S = m.V / np.linalg.norm(m.V, axis=1, keepdims=True)
+    a0 = np.array([0.25, 0.1, -0.3])
+    X = AR.ball_automorphism(a0, S)
+    a, before, after, evals, Y = AR.area_step(m.V, m.F, X, "sphere")
+    assert before > 0.1 and after < 1e-6, (before, after)
+    assert np.abs(a + a0).max() < 1e-5, a
+    idx = np.arange(0, m.nv, 7)
+    assert np.abs(Y[idx] @ Y[idx].T - S[idx] @ S[idx].T).max() < 1e-5   # a rotation of the input
