@@ -387,7 +387,7 @@ def main():
         ea1.record(ctx.stream)
         torch.cuda.synchronize()
         area = {"ms": ea0.elapsed_time(ea1), "evals": ra["evals"], "mean_abs_d_area_before": ra["before"],
-                "mean_abs_d_area_after": ra["after"], "alpha": [ra["param_re"], ra["param_im"]]}
+                "mean_abs_d_area_after": ra["after"], "alpha": ra["param3"][:2]}
         part_a.free()
     batched = None
     if batch_meshes is not None:

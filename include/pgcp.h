@@ -228,30 +228,36 @@ pgcp_status pgcp_metrics(pgcp_ctx* ctx, const pgcp_part* part, const double* U, 
 /*
  * Area distortion (Section 6.2): per face
  *   d_area(T) = ln( (Area(U(T)) / sum Area(U(T'))) / (Area(T) / sum Area(T')) ),
- * Area(U(T)) the planar parameter triangle's signed area, Area(T) the surface
- * triangle's.  mean_abs: host array, one mean |d_area| per mesh of the part
- * (NaN for a mesh dropped by the welding, or with a non-positive parameter
- * area).  U: device, [nv_total*2]; planar results only (a sphere part gives
- * PGCP_E_ARG).  Sums run in a fixed order: repeated calls give the same bits.
+ * Area(U(T)) the parameter triangle's area (planar: signed area; sphere: the
+ * chordal triangle's area, negative when it faces inwards), Area(T) the
+ * surface triangle's.  mean_abs: host array, one mean |d_area| per mesh of the
+ * part (NaN for a mesh dropped by the welding, or with a non-positive
+ * parameter area).  U: device, [nv_total*2] (open parts) or [nv_total*3]
+ * (closed parts).  Sums run in a fixed order: repeated calls give the same bits.
  */
 pgcp_status pgcp_area_distortion(pgcp_ctx* ctx, const pgcp_part* part, const double* U, double* mean_abs);
 
 /* Result of the Mobius area step for one mesh. */
 typedef struct {
-    double  param_re, param_im;   /* alpha (disk) or q (free boundary); 0 = identity */
+    double  param[3];             /* (Re, Im, 0) of alpha (disk) or q (free boundary);
+                                     a (sphere); all 0 = identity */
     double  before, after;        /* mean |d_area| before and after the step */
     int32_t evals;                /* objective evaluations of the search */
     int32_t status;               /* pgcp_status of this mesh (NUMERIC: dropped or folded input) */
 } pgcp_area_result;
 
 /*
- * Mobius area step (Section 6.2): composes each mesh's planar map U (device,
- * [nv_total*2], updated in place) with the Mobius transformation that
- * minimises mean |d_area| over
+ * Mobius area step (Section 6.2): composes each mesh's map U (device,
+ * [nv_total*2] or [nv_total*3], updated in place) with the Mobius
+ * transformation that minimises mean |d_area| over
  *   variant PGCP_DISK: the disk automorphisms (z - alpha) / (1 - conj(alpha) z), |alpha| < 1;
  *   variant PGCP_FREE: the maps z / (1 - q z) (every Mobius map is one of these
- *                      followed by a similarity, which leaves d_area unchanged).
- * The search is Nelder-Mead on the two real parameters from the identity
+ *                      followed by a similarity, which leaves d_area unchanged);
+ *   variant PGCP_SPHERE (closed parts): the ball automorphisms
+ *                      T_a(x) = ((1 - |a|^2)(x - a) - |x - a|^2 a) / (1 - 2<a,x> + |a|^2 |x|^2),
+ *                      |a| < 1 (every conformal map of the sphere is one of these
+ *                      followed by a rotation, which leaves chordal areas unchanged).
+ * The search is Nelder-Mead on the real parameters (2 or 3) from the identity
  * (reflection 1, expansion 2, contraction and shrink 1/2, initial edge 0.05;
  * stops when the simplex spans < 1e-9 and its values < 1e-12, or after 500
  * iterations).  Parameters outside |alpha| < 1, or that give a face a

@@ -64,14 +64,14 @@ class Distortion(C.Structure):
 
 
 class AreaResult(C.Structure):
-    _fields_ = [("param_re", C.c_double), ("param_im", C.c_double), ("before", C.c_double), ("after", C.c_double),
+    _fields_ = [("param", C.c_double * 3), ("before", C.c_double), ("after", C.c_double),
                 ("evals", C.c_int32), ("status", C.c_int32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["param"] = complex(self.param_re, self.param_im)
-        d["status"] = STATUS.get(self.status, str(self.status))
-        return d
+        """param: complex alpha or q (planar); param3: the three stored values (a for the sphere)."""
+        return {"param": complex(self.param[0], self.param[1]), "param3": list(self.param),
+                "before": self.before, "after": self.after, "evals": self.evals,
+                "status": STATUS.get(self.status, str(self.status))}
 
 
 # exported symbols and their signatures (name -> (restype, argtypes))

@@ -5,7 +5,9 @@ the C ABI, against the oracle (oracle/area.py):
   back: the inverse parameter, d_area ~ 0;
 * on pipeline outputs the step takes the oracle's parameter and reaches its
   objective, and maps U as the oracle's formula does;
-* a batch gives each mesh its single-mesh result; a sphere is refused.
+* a batch gives each mesh its single-mesh result;
+* on the sphere (ball automorphisms, chordal areas) the same checks, and a
+  variant that does not fit the part is refused.
 """
 import numpy as np
 import pytest
@@ -73,7 +75,7 @@ def test_step_matches_the_oracle_on_pipeline_output(api, variant):
     assert np.abs(U.cpu().numpy() - np.stack([w.real, w.imag], axis=1)).max() < 1e-12
 
 
-def test_batch_equals_single_meshes_and_sphere_is_refused(api):
+def test_batch_equals_single_meshes(api):
     ms = [meshgen.heightfield_disk_mesh(3000 + 1500 * i, seed=40 + i, nx=2, ny=2) for i in range(2)]
     singles, Us = [], []
     for x in ms:
@@ -86,9 +88,48 @@ def test_batch_equals_single_meshes_and_sphere_is_refused(api):
     rb = part.area_mobius(U, api.DISK)
     for i in range(len(ms)):
         assert rb[i]["param"] == singles[i]["param"] and rb[i]["after"] == singles[i]["after"]
-    s = meshgen.icosphere_sh_mesh(subdiv=2, seed=1)
-    sc = api.Context(variant=api.SPHERE)
-    sp = sc.partition(s.V, s.F, face_labels=s.face_labels, closed=True)
+
+
+def _sphere_part(api, m):
+    ctx = api.Context(variant=api.SPHERE, precision=api.FP32_REFINED, tol=1e-12)
+    return ctx, ctx.partition(m.V, m.F, face_labels=m.face_labels, closed=True)
+
+
+def test_sphere_known_automorphism_is_undone(api):
+    m = meshgen.icosphere_sh_mesh(subdiv=3, seed=0, amp=0.0)
+    S = m.V / np.linalg.norm(m.V, axis=1, keepdims=True)
+    a0 = np.array([0.25, 0.1, -0.3])
+    ctx, part = _sphere_part(api, m)
+    U = torch.tensor(AR.ball_automorphism(a0, S), device="cuda")
+    r = part.area_mobius(U, api.SPHERE)[0]
+    assert r["status"] == "OK" and r["before"] > 0.1 and r["after"] < 1e-6, r
+    assert np.abs(np.array(r["param3"]) + a0).max() < 1e-5
+    Y = U.cpu().numpy()
+    idx = np.arange(0, m.nv, 7)
+    assert np.abs(Y[idx] @ Y[idx].T - S[idx] @ S[idx].T).max() < 1e-5
+
+
+def test_sphere_step_matches_the_oracle_and_wrong_variants_are_refused(api):
+    m = meshgen.icosphere_sh_mesh(subdiv=4, seed=2)
+    ctx, part = _sphere_part(api, m)
+    part.local_param()
+    part.weld()
+    U = part.global_solve()
+    U0 = U.cpu().numpy()
+    got = part.area_distortion(U)[0]
+    assert abs(got - np.abs(AR.sphere_area_distortion(m.V, m.F, U0)).mean()) < 1e-12 * max(1.0, got)
+    r = part.area_mobius(U, api.SPHERE)[0]
+    a, before, after, evals, Y = AR.area_step(m.V, m.F, U0, "sphere")
+    assert r["status"] == "OK" and abs(r["before"] - before) < 1e-12 * before
+    assert abs(r["after"] - after) < 1e-9 * before and r["after"] <= r["before"]
+    assert np.abs(np.array(r["param3"]) - a).max() < 1e-5, (r["param3"], a)
+    assert np.abs(U.cpu().numpy() - AR.ball_automorphism(np.array(r["param3"]), U0)).max() < 1e-12
+    assert np.abs(np.linalg.norm(U.cpu().numpy(), axis=1) - 1.0).max() < 1e-13
     with pytest.raises(api.PgcpError) as e:
-        sp.area_distortion(torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda"))
+        part.area_mobius(U, api.DISK)
+    assert e.value.code == "ARG"
+    d = meshgen.heightfield_disk_mesh(3000, seed=3, nx=2, ny=2)
+    _, dp, DU = _solve(api, d, api.DISK)
+    with pytest.raises(api.PgcpError) as e:
+        dp.area_mobius(DU, api.SPHERE)
     assert e.value.code == "ARG"
