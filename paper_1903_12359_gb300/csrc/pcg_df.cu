@@ -127,7 +127,7 @@ struct ArithF32 {
 constexpr int RUN_THREADS = 256;
 // Iterations per launch of a static-schedule solve; the runs are rebuilt over
 // the unconverged pieces between launches (see df_solve).
-constexpr int REBALANCE_ITERS = 1024;
+constexpr int REBALANCE_ITERS = 256;
 // Resident blocks per SM the kernel is compiled for (MINB): 4 caps it at 64
 // registers (32 warps per SM), 3 at 80 (24 warps, no spills in double-float).
 
