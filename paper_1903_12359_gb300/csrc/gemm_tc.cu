@@ -141,8 +141,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __nv_bfloat16* __r
     ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-collective: all lanes or none
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
-        // warp w reads tensor-memory lanes 32 w .. 32 w + 31 (= tile rows)
+        // warp w reads tensor-memory lanes 32 w .. 32 w + 31 (= tile rows); each
+        // thread writes its row's 16-column chunks with 16-byte stores when the
+        // output rows are 16-byte aligned
         const int64_t row = row0 + warp * 32 + lane;
+        constexpr int64_t CB = EPI == EPI_BIAS_RELU_BF16 ? 2 : 4;   // bytes per output value
+        const bool vecc = (ldc * CB) % 16 == 0 && (reinterpret_cast<uintptr_t>(Cout) & 15) == 0;
+        const bool vecz = (ldz * 4) % 16 == 0 && (reinterpret_cast<uintptr_t>(Zout) & 15) == 0;
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 16) {
             uint32_t r[16];
@@ -156,18 +161,44 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __nv_bfloat16* __r
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             if (row < M) {
+                float v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j;
-                    float v = __uint_as_float(r[j]);
-                    if (EPI == EPI_STORE_F32) {
-                        reinterpret_cast<float*>(Cout)[row * ldc + col] = v;
-                    } else if (EPI == EPI_BIAS_F32) {
-                        reinterpret_cast<float*>(Cout)[row * ldc + col] = v + bias[col];
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + (EPI == EPI_STORE_F32 ? 0.f : bias[c0 + j]);
+                if (EPI == EPI_BIAS_RELU_BF16) {
+                    if (Zout) {
+                        float* zp = Zout + row * ldz + c0;
+                        if (vecz) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                reinterpret_cast<float4*>(zp)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) zp[j] = v[j];
+                        }
+                    }
+                    __nv_bfloat16* cp = reinterpret_cast<__nv_bfloat16*>(Cout) + row * ldc + c0;
+                    if (vecc) {   // 16 values -> two 16-byte stores
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
+                            pk[q] = *reinterpret_cast<const uint32_t*>(&h);
+                        }
+                        reinterpret_cast<uint4*>(cp)[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        reinterpret_cast<uint4*>(cp)[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     } else {
-                        v += bias[col];
-                        if (Zout) Zout[row * ldz + col] = v;
-                        reinterpret_cast<__nv_bfloat16*>(Cout)[row * ldc + col] = __float2bfloat16_rn(fmaxf(v, 0.f));
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) cp[j] = __float2bfloat16_rn(fmaxf(v[j], 0.f));
+                    }
+                } else {
+                    float* cp = reinterpret_cast<float*>(Cout) + row * ldc + c0;
+                    if (vecc) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            reinterpret_cast<float4*>(cp)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) cp[j] = v[j];
                     }
                 }
             }
