@@ -6,8 +6,13 @@
         capped solve ends with PGCP_E_NO_CONVERGENCE, which is expected here
         and reported, not raised.
 `final` the whole pipeline at --n vertices (final solve included).
+`gemm`  one dense layer of the warm-start network on the tensor cores:
+        A [--rows x 128] bf16 times Bt [64 x 128]^T, bias + ReLU to bf16, through
+        the GEMM self-test entry point; three warm-up launches, then --reps
+        timed ones (CUDA events); checked against FP32 torch.
 
 Usage: python -m paper_1903_12359_gb300.profile_cases dncp --n 1000000 --max-iters 300 [--local-precision 0|2]
+       python -m paper_1903_12359_gb300.profile_cases gemm --rows 1048576 --reps 20
 """
 import argparse
 import json
@@ -16,7 +21,9 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["dncp", "final"])
+    ap.add_argument("case", choices=["dncp", "final", "gemm"])
+    ap.add_argument("--rows", type=int, default=1 << 20)
+    ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--max-iters", type=int, default=300)
@@ -27,6 +34,28 @@ def main(argv=None):
     import torch
     from paper_1903_12359_gb300 import api, build, meshgen
     build.build()
+    if a.case == "gemm":
+        M, K, N = a.rows, 128, 64
+        g = torch.Generator(device="cuda").manual_seed(a.seed)
+        A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
+        Bt = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
+        bias = torch.randn((N,), device="cuda", generator=g)
+        ctx = api.Context()
+        for _ in range(3):
+            C = ctx.selftest_gemm_bf16(A, Bt, epilogue=1, bias=bias)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.reps):
+            C = ctx.selftest_gemm_bf16(A, Bt, epilogue=1, bias=bias)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        err = (C.float() - torch.relu(A.float() @ Bt.float().t() + bias)).abs().max().item()
+        print(json.dumps({"case": "gemm", "M": M, "K": K, "N": N, "ms": ms,
+                          "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
+                          "gbs": 2.0 * (M * K + M * N + N * K) / (ms * 1e-3) / 1e9, "max_err": err}))
+        return 0
     m = meshgen.heightfield_disk_mesh(a.n, seed=a.seed, nx=4, ny=2)
     V = torch.as_tensor(m.V, device="cuda")
     F = torch.as_tensor(m.F, device="cuda", dtype=torch.int32)
