@@ -87,16 +87,29 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __nv_bfloat16* __r
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // operand tiles: 16-byte chunks (8 bf16) into the core-matrix layout
-    constexpr int KC = K / 8;   // chunks per row
+    // operand tiles: 16-byte chunks (8 bf16) into the core-matrix layout.  A
+    // warp takes RPG consecutive rows x CG consecutive chunks: each quarter
+    // warp stores 8 rows of one chunk, 128 contiguous bytes (no bank
+    // conflict), and the warp reads whole 32-byte sectors (CG * 16 bytes of
+    // each of its rows).
+    constexpr int KC = K / 8;               // chunks per row
+    constexpr int CG = KC < 4 ? KC : 4;     // chunks per warp step
+    constexpr int RPG = 32 / CG;            // rows per warp step
+    auto chunk_of = [&](int t, int rows, int& m, int& c) {
+        const int grp = t / 32, rg = grp % (rows / RPG), cg = grp / (rows / RPG);
+        m = rg * RPG + t % RPG;
+        c = cg * CG + (t / RPG) % CG;
+    };
     for (int t = threadIdx.x; t < TC_M * KC; t += TC_THREADS) {
-        const int m = t / KC, c = t % KC;
+        int m, c;
+        chunk_of(t, TC_M, m, c);
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (row0 + m < M) v = *reinterpret_cast<const uint4*>(A + (row0 + m) * lda + c * 8);
         *reinterpret_cast<uint4*>(sA + (m >> 3) * SBO_A + c * LBO + (m & 7) * 16) = v;
     }
     for (int t = threadIdx.x; t < N * KC; t += TC_THREADS) {
-        const int n = t / KC, c = t % KC;
+        int n, c;
+        chunk_of(t, N, n, c);
         const uint4 v = *reinterpret_cast<const uint4*>(Bt + (int64_t)n * K + c * 8);
         *reinterpret_cast<uint4*>(sB + (n >> 3) * SBO_A + c * LBO + (n & 7) * 16) = v;
     }
