@@ -68,7 +68,9 @@ typedef struct {
     int32_t pcg_blocks_per_sm;/* resident 256-thread blocks per SM of the mixed-precision PCG kernel:
                                  3 (more registers) or 4 (more warps); autotuner output, 0 = default 4 */
     int32_t pcg_schedule;     /* mixed-precision PCG work schedule: 1 static (each block a fixed row
-                                 range), 2 dynamic (blocks take 256-row chunks from a counter),
+                                 range; the solve runs as launches of 256 iterations and the ranges
+                                 are re-split over the unconverged pieces between them), 2 dynamic
+                                 (blocks take 256-row chunks from a counter),
                                  3 round-robin (block b takes chunks b, b + G, ...; up to 256
                                  pieces, else 1), 4 static with one reduction per iteration
                                  (Chronopoulos-Gear form; up to 16 pieces per block, else 1);
