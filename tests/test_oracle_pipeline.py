@@ -125,3 +125,17 @@ def test_stereographic_charts_agree():
     b = stereo_from_inverted(1.0 / z)
     assert np.abs(a - b).max() < 1e-15
     assert np.abs(np.linalg.norm(a, axis=1) - 1).max() < 1e-15
+
+
+def test_welded_map_is_invariant_to_each_piece_s_rotation_and_scale():
+    """Section 4.3: the first map of Algorithm 1 on a piece depends only on
+    ratios of its points, so multiplying a piece's local coordinates by a
+    complex factor (rotation and scale, which keeps its reference point at 0)
+    leaves the welded, disk and final maps unchanged up to rounding."""
+    m = meshgen.heightfield_disk_mesh(3000, seed=9, nx=2, ny=2)
+    r = pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk")
+    rng = np.random.default_rng(4)
+    factors = [complex(*rng.uniform(0.3, 3.0, 2)) * np.exp(1j * rng.uniform(0, 2 * np.pi)) for _ in r.local]
+    r2 = pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk", local=[f * u for f, u in zip(factors, r.local)])
+    assert r.part.K == 4 and len(r.welds) == 3
+    assert np.abs(r2.out - r.out).max() < 1e-9
