@@ -102,12 +102,15 @@ typedef struct {
     int64_t n_copies;          /* sum of piece vertex counts */
     double  pcg_ms;            /* summed duration of the persistent PCG kernel launches (CUDA events
                                   on the context stream), both solve stages */
-    double  pcg_bytes;         /* algorithmic bytes those launches move, per active free row and
-                                  iteration and per stored entry of its row: 8 + 22*T and 4 + T in the
-                                  mixed-precision kernels (T = 8 double-float, 4 FP32), 4 + 25*T and
-                                  4 + T in the FP64 kernel (T = 8) */
+    double  pcg_bytes;         /* algorithmic bytes of those launches: per active free row and
+                                  iteration 4 + 19*T (row pointer, diagonal, nine vector streams of
+                                  2T), per stored entry 4 + T (T = 8 for FP64 and double-float
+                                  values, 4 for FP32), i.e. 240 B and 136 B a row at 7 entries */
     int32_t pcg_launches;
     int32_t learned_pieces;    /* pieces whose final solve started from the learned prediction */
+    double  pcg_bytes_touched; /* bytes the kernels' schedules actually stream: per row 8 + 22*T
+                                  (mixed precision) or 4 + 25*T (FP64), per entry 4 + T; the gap to
+                                  pcg_bytes is traffic beyond the algorithmic minimum */
 } pgcp_stats;
 
 /* Angle-distortion statistics of a result (Section 5 definition, degrees). */
@@ -135,6 +138,9 @@ pgcp_status pgcp_set_options(pgcp_ctx* ctx, const pgcp_options* opt);
 const char* pgcp_last_error(const pgcp_ctx* ctx);
 /* Number of kernels the library has launched in this process (all contexts). */
 int64_t pgcp_launch_count(void);
+/* Number of device allocations the library has requested in this process (all
+ * contexts; every stream-ordered cudaMallocAsync of its buffers counts). */
+int64_t pgcp_alloc_count(void);
 const char* pgcp_status_string(pgcp_status s);
 
 /*

@@ -235,32 +235,64 @@ def stereo_from_inverted(w: np.ndarray) -> np.ndarray:
     return np.stack([2.0 * x / d, 2.0 * y / d, (1.0 - r2) / d], axis=1)
 
 
+def _local_piece(args):
+    """Cotangent Laplacian and DNCP map of one piece (a pool task)."""
+    X, Fl, ll = args
+    L = cotan_laplacian(X, Fl)
+    u, ref = dncp(X, Fl, ll, L)
+    return L, u, ref
+
+
+def _final_piece(args):
+    """Laplace solve of one piece with its welded boundary (a pool task)."""
+    L, ll, ub = args
+    return harmonic_solve(L, ll, ub)
+
+
 def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
-         map_interior: bool = False, local=None) -> Result:
+         map_interior: bool = False, local=None, workers: int = 1) -> Result:
     """Run Algorithm 3.  ``variant`` is "free", "disk" or "sphere".
 
     ``local`` (tests only): per-piece complex coordinates to use instead of the
     DNCP solve, so the welding can be compared on identical inputs.
+    ``workers`` > 1: the per-piece DNCP and Laplace solves run in a pool of that
+    many spawned processes, one piece per task -- the parallel scheme of the
+    paper's experiments (one subdomain per parallel worker, Section 5.6).  The
+    arithmetic of every piece is the same as with workers = 1.
     """
     V = np.asarray(V, dtype=np.float64)
     P = partition(V, F, cut_edges=cut_edges, face_labels=face_labels)
     welds = weld_schedule(P, closed_surface=(variant == "sphere"))
     res = Result(part=P, welds=welds)
-    loop_local = []
+    pool = None
+    if workers > 1 and P.K > 1:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(workers, P.K))
+    try:
+        return _pgcp_stages(res, V, P, welds, variant, map_interior, local, pool)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+
+
+def _pgcp_stages(res, V, P, welds, variant, map_interior, local, pool):
+    loop_local = [np.searchsorted(P.verts[i], P.loops[i]) for i in range(P.K)]
+    if local is None:
+        tasks = [(V[P.verts[i]], P.local_F[i], loop_local[i]) for i in range(P.K)]
+        solved = pool.map(_local_piece, tasks, chunksize=1) if pool is not None else [_local_piece(t) for t in tasks]
     for i in range(P.K):
-        X = V[P.verts[i]]
-        L = cotan_laplacian(X, P.local_F[i])
-        ll = np.searchsorted(P.verts[i], P.loops[i])
+        ll = loop_local[i]
         if local is None:
-            u, ref = dncp(X, P.local_F[i], ll, L)
+            L, u, ref = solved[i]
         else:
+            L = cotan_laplacian(V[P.verts[i]], P.local_F[i])
             u, ref = np.asarray(local[i], dtype=np.complex128), -1
         res.L.append(L)
         res.local.append(u)
         res.ref.append(ref)
         res.welded.append(u.copy())
         res.welded_inf.append(np.zeros(u.size, dtype=bool))
-        loop_local.append(ll)
     for wd in welds:
         _weld_once(res, wd, map_interior, sphere_close=wd.closed)
     if variant == "sphere":
@@ -268,11 +300,13 @@ def pgcp(V, F, cut_edges=None, face_labels=None, variant: str = "disk",
     if variant == "disk":
         _disk_step(res, map_interior)
     # final Laplace solves with the welded boundary
+    tasks = []
     for i in range(P.K):
         ub = res.welded[i][loop_local[i]]
         if np.any(res.welded_inf[i][loop_local[i]]) or not np.all(np.isfinite(ub)):
             raise OracleError("NUMERIC", f"piece {i}: non-finite welded boundary")
-        res.final.append(harmonic_solve(res.L[i], loop_local[i], ub))
+        tasks.append((res.L[i], loop_local[i], ub))
+    res.final = pool.map(_final_piece, tasks, chunksize=1) if pool is not None else [_final_piece(t) for t in tasks]
     # gather: lowest label wins
     nv = V.shape[0]
     if variant == "sphere":

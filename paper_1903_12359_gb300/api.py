@@ -49,7 +49,8 @@ class Stats(C.Structure):
                 ("final_relres", C.c_double), ("seam_mismatch", C.c_double), ("ms_partition", C.c_double),
                 ("ms_assembly", C.c_double), ("ms_local", C.c_double), ("ms_weld", C.c_double),
                 ("ms_final", C.c_double), ("nnz", C.c_int64), ("n_copies", C.c_int64), ("pcg_ms", C.c_double),
-                ("pcg_bytes", C.c_double), ("pcg_launches", C.c_int32), ("learned_pieces", C.c_int32)]
+                ("pcg_bytes", C.c_double), ("pcg_launches", C.c_int32), ("learned_pieces", C.c_int32),
+                ("pcg_bytes_touched", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +85,7 @@ SIGNATURES = {
     "pgcp_last_error": (C.c_char_p, [_P]),
     "pgcp_status_string": (C.c_char_p, [C.c_int]),
     "pgcp_launch_count": (C.c_int64, []),
+    "pgcp_alloc_count": (C.c_int64, []),
     "pgcp_partition": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, C.c_int32,
                                  C.POINTER(_P)]),
     "pgcp_partition_batch": (C.c_int, [_P, C.c_int32, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(_P),
@@ -152,12 +154,37 @@ def launch_count() -> int:
     return int(load().pgcp_launch_count())
 
 
+def alloc_count() -> int:
+    """Device allocations the library has requested so far in this process."""
+    return int(load().pgcp_alloc_count())
+
+
 def default_options(**kw) -> Options:
     o = Options()
     load().pgcp_default_options(C.byref(o))
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def check_coords(U, nv: int, closed: bool, device=None, inplace: bool = False):
+    """Refuse, before any launch, a coordinate tensor the kernels cannot read
+    safely: it must be a float64 tensor of shape (nv, 3) for a closed part and
+    (nv, 2) otherwise, on the CUDA device the context is bound to (and
+    contiguous when it is updated in place)."""
+    dim = 3 if closed else 2
+    if not isinstance(U, torch.Tensor):
+        raise ValueError("coordinates must be a torch tensor")
+    if U.dtype != torch.float64:
+        raise ValueError(f"coordinates must be float64, got {U.dtype}")
+    if tuple(U.shape) != (nv, dim):
+        raise ValueError(f"coordinates must have shape ({nv}, {dim}), got {tuple(U.shape)}")
+    if not U.is_cuda:
+        raise ValueError("coordinates must be a CUDA tensor")
+    if device is not None and U.device.index != device:
+        raise ValueError(f"coordinates are on cuda:{U.device.index}, the context on cuda:{device}")
+    if inplace and not U.is_contiguous():
+        raise ValueError("coordinates updated in place must be contiguous")
 
 
 def _ptr(t):
@@ -182,6 +209,7 @@ class Context:
         lib = load()
         self.options = options if options is not None else default_options(**kw)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.cuda.current_device()
         h = C.c_void_p()
         st = lib.pgcp_create(C.byref(h), C.byref(self.options), C.c_void_p(self.stream.cuda_stream))
         if st:
@@ -393,12 +421,14 @@ class Part:
         return out
 
     def metrics(self, U):
+        check_coords(U, self.nv, self.closed, self.ctx.device)
         m = Distortion()
         self.ctx.check(load().pgcp_metrics(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
         return m.as_dict()
 
     def area_distortion(self, U):
         """pgcp_area_distortion: mean |d_area| (Section 6.2) of each mesh's planar map U."""
+        check_coords(U, self.nv, self.closed, self.ctx.device)
         n = self.info()["n_mesh"]
         out = (C.c_double * n)()
         self.ctx.check(load().pgcp_area_distortion(self.ctx.h, self.h, _ptr(U.contiguous()), out))
@@ -407,8 +437,7 @@ class Part:
     def area_mobius(self, U, variant):
         """pgcp_area_mobius: the Mobius area step (Section 6.2) on U in place
         (a contiguous float64 CUDA tensor); one result dict per mesh."""
-        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.is_contiguous() and U.dtype == torch.float64):
-            raise ValueError("U must be a contiguous float64 CUDA tensor (updated in place)")
+        check_coords(U, self.nv, self.closed, self.ctx.device, inplace=True)
         n = self.info()["n_mesh"]
         out = (AreaResult * n)()
         self.ctx.check(load().pgcp_area_mobius(self.ctx.h, self.h, _ptr(U), int(variant), out))
@@ -418,6 +447,7 @@ class Part:
         """pgcp_metrics_noalloc: the same statistics with no device allocation,
         for callers that must not allocate (parts of at most
         METRICS_NOALLOC_MAX_FACES faces; calls must not overlap in time)."""
+        check_coords(U, self.nv, self.closed, self.ctx.device)
         m = Distortion()
         self.ctx.check(load().pgcp_metrics_noalloc(self.ctx.h, self.h, _ptr(U.contiguous()), C.byref(m)))
         return m.as_dict()

@@ -29,6 +29,8 @@ void fail(pgcp_status code, const std::string& msg) { throw Thrown(code, msg); }
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static std::atomic<long long> g_allocs{0};
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void check_cuda(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return;
@@ -233,6 +235,7 @@ pgcp_status pgcp_set_options(pgcp_ctx* ctx, const pgcp_options* opt) {
 }
 
 int64_t pgcp_launch_count(void) { return (int64_t)g_launches.load(); }
+int64_t pgcp_alloc_count(void) { return (int64_t)g_allocs.load(); }
 
 const char* pgcp_last_error(const pgcp_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 

@@ -511,7 +511,8 @@ void launch_pcg_lanes(pgcp_ctx* ctx, Part& P, PcgArgs<T> a) {
     // per free row and iteration: row pointer 4 B, inverse diagonal T (phase 2),
     // vectors 2T each: z read (1) and write (1), r r/w (2), p r/w + read (3),
     // q r/w + read (3), x r/w (2) -> 24T; per stored entry: column 4 B + value T
-    P.stats.pcg_bytes += (double)w[0] * (4.0 + 25.0 * Tb) + (double)w[1] * (4.0 + Tb);
+    P.stats.pcg_bytes += (double)w[0] * (4.0 + 19.0 * Tb) + (double)w[1] * (4.0 + Tb);
+    P.stats.pcg_bytes_touched += (double)w[0] * (4.0 + 25.0 * Tb) + (double)w[1] * (4.0 + Tb);
     P.stats.pcg_launches += 1;
 }
 

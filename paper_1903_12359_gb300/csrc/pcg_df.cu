@@ -1869,12 +1869,16 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     unsigned long long w[2] = {0, 0};
     PGCP_CUDA(cudaMemcpyAsync(w, D.work.p, sizeof(w), cudaMemcpyDeviceToHost, s));
     PGCP_CUDA(cudaStreamSynchronize(s));
-    // Per free row and iteration, with vector pairs of 2T bytes (T = 8 for
-    // double-float, 4 for FP32): phase B row pointer 4, r 2T, p r/w 4T,
-    // q r/w 4T; phase A diagonal 4, x r/w 4T, r r/w 4T, p 2T, q 2T
-    // -> 8 + 22T.  Per stored entry: column 4 + value T (gathered r hits cache).
+    // Algorithmic bytes (the minimal streams of one 2-RHS Jacobi-PCG iteration,
+    // T = 8 for FP64-width double-float values, 4 for FP32): per free row the
+    // row pointer 4, the diagonal T and nine vector streams of 2T (gathered
+    // operand, q written and read, x read and written, r read and written, p
+    // read and written) -> 4 + 19T; per stored entry column 4 + value T.  At
+    // seven entries a row that is 240 B (double-float) and 136 B (FP32).
+    // Touched bytes (what this kernel's schedule streams): per row 8 + 22T.
     const double T = D.f32 ? 4.0 : 8.0;
-    P.stats.pcg_bytes += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
+    P.stats.pcg_bytes += (double)w[0] * (4.0 + 19.0 * T) + (double)w[1] * (4.0 + T);
+    P.stats.pcg_bytes_touched += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
     return it;
 }
 

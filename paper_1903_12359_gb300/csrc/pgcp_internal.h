@@ -22,6 +22,8 @@ struct Error {
 [[noreturn]] void fail(pgcp_status code, const std::string& msg);
 // Counts every kernel launch of the library (pgcp_launch_count()).
 void note_launch();
+// Counts every device allocation of the library (pgcp_alloc_count()).
+void note_alloc();
 void check_cuda(cudaError_t e, const char* what);
 #define PGCP_CUDA(call) ::pgcp::check_cuda((call), #call)
 
@@ -91,6 +93,7 @@ struct DBuf {
         n = count;
         if (count == 0) return;
         cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+        note_alloc();
         if (e != cudaSuccess) {
             p = nullptr;
             n = 0;

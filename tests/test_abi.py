@@ -71,3 +71,25 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert int(val) == want, (cname, what, int(val), want)
     o = api.default_options()
     assert o.deterministic == 0 and o.local_precision == api.DF64_REFINED
+
+
+def test_coordinate_tensors_are_checked_before_any_launch():
+    """metrics, area and no-alloc entry points read U as float64 [nv][dim]: the
+    binding refuses another dtype, shape or a host tensor before it calls the
+    library (no GPU is touched here)."""
+    import torch
+    from paper_1903_12359_gb300 import api
+    nv = 10
+    for closed, dim in ((False, 2), (True, 3)):
+        with pytest.raises(ValueError, match="float64"):
+            api.check_coords(torch.zeros((nv, dim), dtype=torch.float32), nv, closed)
+        with pytest.raises(ValueError, match="shape"):
+            api.check_coords(torch.zeros((nv, 5 - dim), dtype=torch.float64), nv, closed)
+        with pytest.raises(ValueError, match="shape"):
+            api.check_coords(torch.zeros((nv + 1, dim), dtype=torch.float64), nv, closed)
+        with pytest.raises(ValueError, match="shape"):
+            api.check_coords(torch.zeros(nv * dim, dtype=torch.float64), nv, closed)
+        with pytest.raises(ValueError, match="CUDA"):
+            api.check_coords(torch.zeros((nv, dim), dtype=torch.float64), nv, closed)
+    with pytest.raises(ValueError, match="tensor"):
+        api.check_coords([[0.0, 0.0]] * nv, nv, False)

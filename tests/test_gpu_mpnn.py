@@ -21,8 +21,8 @@ def api():
     return a
 
 
-def _solved_part(api, m, warm=1, gnn=None):
-    ctx = api.Context(variant=api.DISK, precision=0, tol=1e-12, warm_start=warm)
+def _solved_part(api, m, warm=1, gnn=None, interior_fp64=0):
+    ctx = api.Context(variant=api.DISK, precision=0, tol=1e-12, warm_start=warm, interior_map_fp64=interior_fp64)
     if gnn is not None:
         ctx.set_gnn(gnn)
     part = ctx.partition(m.V, m.F, face_labels=m.face_labels)
@@ -32,21 +32,22 @@ def _solved_part(api, m, warm=1, gnn=None):
     return ctx, part, out
 
 
-def _oracle_graph(part):
-    """Block-diagonal Laplacian of the part (GPU CSR, values equal to the
-    oracle's cotan Laplacian within 1e-13), boundary flags, piece of each row."""
-    rp, col, val = [t.cpu().numpy() for t in part.csr()]
-    n = rp.size - 1
-    fl, voff, verts, loff, loops = [t.cpu().numpy() for t in part.partition_arrays()]
-    # the C ABI returns columns local to each piece: shift them to global rows
-    row_base = np.repeat(voff[:-1], np.diff(voff))
-    L = csr_matrix((val, col + np.repeat(row_base, np.diff(rp)), rp), shape=(n, n))
-    is_bnd = np.zeros(n, dtype=bool)
-    for i in range(voff.size - 1):
-        lv = loops[loff[i]:loff[i + 1]]
-        rows = voff[i] + np.searchsorted(verts[voff[i]:voff[i + 1]], lv)
-        is_bnd[rows] = True
-    return L, is_bnd, voff
+def _oracle_graph(m):
+    """The oracle's own pipeline on the mesh (Algorithm 3 with the interior
+    mapped through the welding chains): block-diagonal cotan Laplacian of the
+    pieces, boundary flags, row offsets of the pieces and the weld map u_w of
+    every vertex copy, all computed by the oracle."""
+    from scipy.sparse import block_diag
+    from oracle.pipeline import pgcp as o_pgcp
+    ref = o_pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk", map_interior=True)
+    P = ref.part
+    L = block_diag(ref.L).tocsr()
+    voff = np.concatenate([[0], np.cumsum([v.size for v in P.verts])])
+    is_bnd = np.zeros(voff[-1], dtype=bool)
+    for i in range(P.K):
+        is_bnd[voff[i] + np.searchsorted(P.verts[i], P.loops[i])] = True
+    c = np.concatenate(ref.welded)
+    return L, is_bnd, voff, np.column_stack([c.real, c.imag])
 
 
 def _bf16(x):
@@ -68,10 +69,11 @@ def _theta_as_gpu_uses(theta):
 @pytest.fixture(scope="module")
 def case(api):
     m = meshgen.heightfield_disk_mesh(3000, seed=3, nx=4, ny=2)
-    ctx, part, out = _solved_part(api, m)
-    L, is_bnd, voff = _oracle_graph(part)
-    c = part.coords(1).cpu().numpy()
-    uw = np.column_stack([c.real, c.imag])
+    # FP64 interior weld map on the GPU, as in the oracle
+    ctx, part, out = _solved_part(api, m, interior_fp64=1)
+    L, is_bnd, voff, uw = _oracle_graph(m)
+    gv = part.partition_arrays()[1].cpu().numpy()
+    assert np.array_equal(gv, voff)              # the same pieces, rows in the same order
     return dict(m=m, ctx=ctx, part=part, L=L, is_bnd=is_bnd, voff=voff, uw=uw)
 
 
@@ -110,7 +112,9 @@ def test_prediction_and_gradient_match_oracle(api, case):
     ref[inner] += s_row[inner, None] * out[inner, 0:2]
     corr = np.abs(ref[inner] - case["uw"][inner]).max()
     assert np.abs(x0[inner] - ref[inner]).max() <= 5e-2 * corr
-    assert np.array_equal(x0[~inner], case["uw"][~inner])
+    # boundary rows keep the welded values (GPU FP64 welds of the GPU DNCP map
+    # against the oracle's welds of its direct solve)
+    assert np.abs(x0[~inner] - case["uw"][~inner]).max() < 1e-9
     # gradient: per parameter block, relative L2 error of the BF16 network
     g, loss = gnn.grad(part)
     go = om.gradient(th, F, P, T, inner)

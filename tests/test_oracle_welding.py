@@ -178,20 +178,53 @@ def test_weld_maps_pair_up_the_arc():
     gB, B = W.intermediate_form(_pts(zb[:k + 1]), k, -1.0)
     hs, X, Y = W.weld_maps(A, B, k)
     assert len(hs) == k
-    # each h_j sends its own pair (alpha_j, beta_j) to 0 up to rounding: recompute
-    # alpha_j, beta_j by the chain without the index rule and check they close
+    # Algorithm 2's postcondition: after the whole chain the two images of every
+    # shared arc point coincide, a~_j = b~_j for 1 <= j <= k (a_0 = b_0 goes to
+    # infinity on both sides), to 1e-10 relative
+    assert X.inf[0] and Y.inf[0]
+    xa, yb = X.complex()[1:k + 1], Y.complex()[1:k + 1]
+    rel = np.abs(xa - yb) / np.maximum(np.abs(xa), 1.0)
+    assert rel.max() < 1e-10, rel.max()
+    # each h_j closes its own pair: recomputed by the chain without the index
+    # rule, alpha_j and beta_j land at 0 up to the rounding of that evaluation
     for j in (k - 1, k // 2, 1):
         a = W.apply_chain(hs[:k - 1 - j], A.take([j]))
         b = W.apply_chain(hs[:k - 1 - j], B.take([j]))
         ha = W.apply_rec(hs[k - 1 - j], a).complex()[0]
         hb = W.apply_rec(hs[k - 1 - j], b).complex()[0]
         assert abs(ha) < 1e-6 and abs(hb) < 1e-6
-    # the non-arc points of A and of B end up on different sides of the seam:
-    # after the welding, the two loops' images do not cross (checked by the
-    # pipeline's fold test); here: all other points stay finite
-    ra = W.apply_chain(gA + hs, _pts(z[k + 1:]))
-    rb = W.apply_chain(gB + hs, _pts(zb[k + 1:]))
-    assert np.all(np.isfinite(ra.complex())) and np.all(np.isfinite(rb.complex()))
+
+
+def test_weld_puts_the_two_pieces_on_opposite_sides_of_the_seam():
+    """After the weld of the small disk case (two pieces, Algorithm 2 plus the
+    normalisation), every face of both pieces keeps a positive signed area
+    (interior points mapped through their side's chain) and the faces together
+    cover the region bounded by the image of the outer loop exactly once: the
+    sum of the face areas equals that loop's polygon area.  If the two pieces
+    landed on the same side of the seam their images would overlap and the sum
+    would exceed the polygon area."""
+    m = meshgen.polar_disk_mesh()
+    from oracle.pipeline import pgcp as o_pgcp
+    res = o_pgcp(m.V, m.F, face_labels=m.face_labels, variant="free", map_interior=True)
+    P = res.part
+    total = 0.0
+    for i in range(P.K):
+        z = res.welded[i]
+        assert not res.welded_inf[i].any()
+        Fl = P.local_F[i]
+        a, b, c = z[Fl[:, 0]], z[Fl[:, 1]], z[Fl[:, 2]]
+        area = 0.5 * ((b - a).real * (c - a).imag - (b - a).imag * (c - a).real)
+        assert area.min() > 0.0
+        total += float(area.sum())
+    outer = res.welds[-1].new_loop
+    pos = {}
+    for i in range(P.K):
+        for li, g in enumerate(P.verts[i].tolist()):
+            pos.setdefault(g, (i, li))
+    w = np.array([res.welded[pos[g][0]][pos[g][1]] for g in outer.tolist()])
+    poly = 0.5 * float(np.sum(w.real * np.roll(w.imag, -1) - w.imag * np.roll(w.real, -1)))
+    assert poly > 0.0
+    assert abs(total - poly) < 1e-9 * poly, (total, poly)
 
 
 def test_geodesic_disk_converges_to_rotation_on_a_circle():

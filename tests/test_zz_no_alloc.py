@@ -49,8 +49,11 @@ def test_noalloc_metrics_equal_pooled_metrics_twice(api, kind):
         m, variant = meshgen.icosphere_sh_mesh(subdiv=3, seed=1), 2
     ctx, part, out = _solved(api, m, variant)
     ref = part.metrics(out)
+    a0 = api.alloc_count()
     first = part.metrics_noalloc(out)
     second = part.metrics_noalloc(out)
+    # the library's own counter of device allocations does not move
+    assert api.alloc_count() == a0
     _compare(ref, first)
     _compare(ref, second)
     assert ref["n_corners"] == 3 * m.nf
