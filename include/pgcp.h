@@ -83,7 +83,11 @@ typedef struct {
                                  available with PGCP_FP64 in either solve stage (PGCP_E_ARG).
                                  0 (default): unordered atomic sums, which may differ in the last
                                  bits between runs and change the iteration count slightly. */
-    int32_t reserved[2];
+    int32_t local_precond;    /* preconditioner of the double-float DNCP solve (static schedule, not
+                                 deterministic): 0 (default) multilevel -- additive corrections by
+                                 low-degree polynomials on nested blocks of 16 * 4^l rows of every
+                                 piece -- or 1 Jacobi only.  Other solver settings always use Jacobi. */
+    int32_t reserved[1];
 } pgcp_options;
 
 /* Per-call statistics (host struct, filled by pgcp_global_solve). */
@@ -329,7 +333,9 @@ pgcp_status pgcp_part_mesh_status(const pgcp_part* part, int32_t* status);
  * stores the fastest in the context options (and in *chosen):
  *   mixed-precision local solves: pcg_blocks_per_sm in {3, 4} x pcg_schedule
  *   in {static, dynamic, round-robin, one reduction};  FP64 local solves: spmv_lanes in {1, 2, 4} x
- *   block_rows_log2 in {8, 9, 10}.
+ *   block_rows_log2 in {8, 9, 10}.  With the multilevel preconditioner (double-float local solves,
+ *   local_precond 0, not deterministic) the static schedule is the only candidate: the other
+ *   schedules run without the preconditioner, and a time per iteration does not compare them.
  * The probes overwrite the part's local map: call pgcp_local_param afterwards.
  * ms_per_iter (may be NULL): the winner's kernel time per iteration.
  */

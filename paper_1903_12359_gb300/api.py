@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("warm_start", C.c_int32),
                 ("interior_map_fp64", C.c_int32), ("block_rows_log2", C.c_int32), ("local_precision", C.c_int32),
                 ("spmv_lanes", C.c_int32), ("pcg_blocks_per_sm", C.c_int32),
-                ("pcg_schedule", C.c_int32), ("deterministic", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("pcg_schedule", C.c_int32), ("deterministic", C.c_int32), ("local_precond", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class Stats(C.Structure):

@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpgcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["primitives.cu", "partition.cu", "schedule.cu", "assemble.cu", "pcg.cu", "pcg_df.cu", "weld.cu", "solve.cu",
-           "metrics.cu", "area.cu", "gemm_tc.cu", "mpnn.cu", "api.cu"]
+SOURCES = ["primitives.cu", "partition.cu", "schedule.cu", "assemble.cu", "pcg.cu", "pcg_df.cu", "pcg_ml.cu", "weld.cu",
+           "solve.cu", "metrics.cu", "area.cu", "gemm_tc.cu", "mpnn.cu", "api.cu"]
 NO_FMA = {"weld.cu"}
 
 
@@ -41,6 +41,7 @@ def _flags(src: str) -> list:
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "pgcp_internal.h"),
+                                                         os.path.join(CSRC, "df_arith.cuh"),
                                                          os.path.join(ROOT, "include", "pgcp.h"),
                                                          os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)

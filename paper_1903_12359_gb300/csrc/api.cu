@@ -552,6 +552,11 @@ pgcp_status pgcp_autotune(pgcp_ctx* ctx, pgcp_part* part, int32_t probe_iters, p
         if (saved.local_precision == PGCP_FP64) {
             for (int lanes : {1, 2, 4})
                 for (int rows : {8, 9, 10}) cands.push_back(Cand{saved.pcg_blocks_per_sm, saved.pcg_schedule, lanes, rows});
+        } else if (saved.local_precision == PGCP_DF64_REFINED && saved.local_precond == 0 && !saved.deterministic) {
+            // the multilevel preconditioner runs on the static schedule only, and the
+            // probes compare time per iteration, which is meaningless across
+            // preconditioners: the static schedule is the one candidate
+            cands.push_back(Cand{saved.pcg_blocks_per_sm, 1, saved.spmv_lanes, saved.block_rows_log2});
         } else {
             // deterministic mode runs the static schedule only
             for (int sched : {1, 2, 3, 4})

@@ -42,6 +42,7 @@
 #include <cmath>
 #include <vector>
 
+#include "df_arith.cuh"
 #include "pgcp_internal.h"
 
 namespace cg = cooperative_groups;
@@ -50,81 +51,8 @@ namespace pgcp {
 
 namespace {
 
-// ---------------------------------------------------------------- double-float
+using namespace dfa;
 
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return make_float2(s, e);
-}
-
-__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-
-// acc + a * b (the lo * lo product, ~2^-48 relative, is dropped)
-__device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    const float2 s = two_sum(acc.x, p);
-    const float t = __fadd_rn(s.y, __fadd_rn(e, acc.y));
-    return fast_two_sum(s.x, t);
-}
-
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-    const float2 s = two_sum(a.x, b.x);
-    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
-}
-
-__device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
-
-__device__ __forceinline__ float2 d_to_df(double d) {
-    const float h = __double2float_rn(d);
-    return make_float2(h, __double2float_rn(d - (double)h));
-}
-
-// Arithmetic policies: one scalar S (also the stored matrix value) and a
-// row's (x, y) pair V.
-// ArithDF: double-float scalars, V = float4 {x.hi, x.lo, y.hi, y.lo}.
-// ArithF32: FP32 scalars, V = float2, FP32 accumulation.
-struct ArithDF {
-    using S = float2;
-    using V = float4;
-    static constexpr int bytes = 8;
-    static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ S fma(S acc, S a, S b) { return df_fma(acc, a, b); }
-    static __device__ __forceinline__ S neg(S a) { return make_float2(-a.x, -a.y); }
-    static __device__ __forceinline__ S cx(V v) { return make_float2(v.x, v.y); }
-    static __device__ __forceinline__ S cy(V v) { return make_float2(v.z, v.w); }
-    static __device__ __forceinline__ V pack(S a, S b) { return make_float4(a.x, a.y, b.x, b.y); }
-    static __device__ __forceinline__ V vzero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-    static __device__ __forceinline__ S from_d(double d) { return d_to_df(d); }
-    static __device__ __forceinline__ double to_d(S a) { return df_to_d(a); }
-    static __device__ __forceinline__ float2 as_df(S a) { return a; }
-    static __device__ __forceinline__ float lead(S a) { return a.x; }
-};
-struct ArithF32 {
-    using S = float;
-    using V = float2;
-    static constexpr int bytes = 4;
-    static __device__ __forceinline__ S zero() { return 0.f; }
-    static __device__ __forceinline__ S fma(S acc, S a, S b) { return fmaf(a, b, acc); }
-    static __device__ __forceinline__ S neg(S a) { return -a; }
-    static __device__ __forceinline__ S cx(V v) { return v.x; }
-    static __device__ __forceinline__ S cy(V v) { return v.y; }
-    static __device__ __forceinline__ V pack(S a, S b) { return make_float2(a, b); }
-    static __device__ __forceinline__ V vzero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ S from_d(double d) { return __double2float_rn(d); }
-    static __device__ __forceinline__ double to_d(S a) { return (double)a; }
-    static __device__ __forceinline__ float2 as_df(S a) { return make_float2(a, 0.f); }
-    static __device__ __forceinline__ float lead(S a) { return a; }
-};
-
-constexpr int RUN_THREADS = 256;
 // Iterations per launch of a static-schedule solve; the runs are rebuilt over
 // the unconverged pieces between launches (see df_solve).
 constexpr int REBALANCE_ITERS = 256;
@@ -216,59 +144,6 @@ __device__ __forceinline__ void ordered_sums(const double* const* src, int r0, i
 __device__ __forceinline__ bool piece_done(const double* RD, const double* THR, int s, int c, bool dncp) {
     if (dncp) return __ldcg(RD + 2 * s) + __ldcg(RD + 2 * s + 1) <= THR[2 * s] + THR[2 * s + 1];
     return __ldcg(RD + 2 * s + c) <= THR[2 * s + c];
-}
-
-// Sum NV double-float values over the block on the FP32 pipe; thread 0 gets
-// the totals as doubles.  red: NV * (warps) float2 of shared memory.
-template <int NV>
-__device__ __forceinline__ void block_sum_df(float2* v, float2* red, double* out) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            float2 t;
-            t.x = __shfl_xor_sync(0xffffffffu, v[i].x, o);
-            t.y = __shfl_xor_sync(0xffffffffu, v[i].y, o);
-            v[i] = df_add(v[i], t);
-        }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = RUN_THREADS / 32;
-    __syncthreads();   // red is free (its previous readers are done)
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) red[NV * warp + i] = v[i];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            float2 t = lane < NW ? red[NV * lane + i] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int o = NW / 2; o > 0; o >>= 1) {
-                float2 u;
-                u.x = __shfl_xor_sync(0xffffffffu, t.x, o);
-                u.y = __shfl_xor_sync(0xffffffffu, t.y, o);
-                t = df_add(t, u);
-            }
-            if (lane == 0) out[i] = df_to_d(t);
-        }
-    }
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* ptr) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
-
-// One stored entry of the SpMV: w += v * r_c (or the cross form).
-template <typename A>
-__device__ __forceinline__ void spmv_entry(int32_t c, typename A::S v, const typename A::V* r, typename A::S& w0,
-                                           typename A::S& w1) {
-    const bool cross = c < 0;
-    const typename A::V rc = r[cross ? ~c : c];
-    const typename A::S a0 = cross ? A::cy(rc) : A::cx(rc);
-    const typename A::S a1 = cross ? A::cx(rc) : A::cy(rc);
-    const typename A::S v0 = cross ? A::neg(v) : v;
-    w0 = A::fma(w0, v0, a0);
-    w1 = A::fma(w1, v, a1);
 }
 
 template <typename A, int MINB>
@@ -1636,10 +1511,13 @@ void finish_typed(pgcp_ctx* ctx, DfSystem& D, double2* x) {
 // ---------------------------------------------------------------- host side
 
 // Row runs of the persistent grid: the rows of the active pieces (all when
-// active is null), concatenated in piece order, split into `grid` equal ranges,
-// each range cut at piece boundaries.  Returns the rows covered.
+// active is null), concatenated in piece order, split into `grid` near-equal
+// ranges, each range cut at piece boundaries.  With align > 1 a split inside a
+// piece is moved down to a multiple of `align` rows from the piece's first row;
+// with maxlen > 0 (a multiple of align) longer runs are cut into pieces of
+// maxlen rows.  Returns the rows covered.
 int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* active, int grid,
-                  std::vector<DfRun>& runs, std::vector<int32_t>& roff) {
+                  std::vector<DfRun>& runs, std::vector<int32_t>& roff, int align, int maxlen) {
     std::vector<int> segs;
     int64_t total = 0;
     for (int i = 0; i + 1 < (int)voff.size(); ++i)
@@ -1653,14 +1531,19 @@ int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* 
     int64_t pos = 0, cbase = 0;   // position in the concatenation; start of piece segs[c] in it
     for (int b = 0; b < grid; ++b) {
         roff[b] = (int32_t)runs.size();
-        const int64_t target = total * (b + 1) / grid;
+        const int64_t target = b + 1 == grid ? total : total * (b + 1) / grid;
         while (pos < target && c < segs.size()) {
             const int seg = segs[c];
             const int64_t len = voff[seg + 1] - voff[seg];
-            const int64_t end = std::min<int64_t>(target, cbase + len);
-            if (end > pos)
-                runs.push_back(DfRun{seg, (int32_t)(voff[seg] + (pos - cbase)), (int32_t)(voff[seg] + (end - cbase)), 0, 0,
+            int64_t end = std::min<int64_t>(target, cbase + len);
+            if (end < cbase + len && align > 1) end = cbase + (end - cbase) / align * align;
+            if (end <= pos) break;   // the aligned split leaves nothing here: the next range takes it
+            for (int64_t a = pos; a < end;) {
+                const int64_t e = maxlen > 0 ? std::min<int64_t>(end, a + maxlen) : end;
+                runs.push_back(DfRun{seg, (int32_t)(voff[seg] + (a - cbase)), (int32_t)(voff[seg] + (e - cbase)), 0, 0,
                                      0, 0, 0});
+                a = e;
+            }
             pos = end;
             if (pos == cbase + len) {
                 cbase += len;
@@ -1687,6 +1570,10 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     D.sched = sched == 0 ? 1 : sched;
     D.det = ctx->opt.deterministic ? 1 : 0;
     if (D.det) D.sched = 1;   // ordered sums are implemented for the static schedule
+    // multilevel preconditioner: double-float DNCP solves on the static schedule
+    const int pc = ctx->opt.local_precond;
+    if (pc != 0 && pc != 1) fail(PGCP_E_ARG, "local_precond must be 0 (multilevel) or 1 (Jacobi)");
+    D.ml = (dncp && !f32 && !D.det && D.sched == 1 && pc == 0) ? 1 : 0;
     if (D.sched == 3 && P.K > RR_MAXSEG) D.sched = 1;   // the round-robin tables hold RR_MAXSEG pieces
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;
@@ -1703,13 +1590,15 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     D.dgn.alloc(n, s);
     if (f32) build_typed<ArithF32>(ctx, P, dncp, fixed, D, cnt.p, off.p);
     else build_typed<ArithDF>(ctx, P, dncp, fixed, D, cnt.p, off.p);
+    if (D.ml) ml_build(ctx, P, fixed, D);
     // persistent grid (all co-resident blocks) and its row runs
-    int grid = (int)std::min<int64_t>((int64_t)D.per_sm * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 32)));
+    const int per_sm = D.ml ? D.ml_per_sm : D.per_sm;
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 32)));
     grid = std::max(grid, 1);
     D.grid = grid;
     std::vector<DfRun> runs;
     std::vector<int32_t> roff;
-    D.covered = make_runs(P.voff, nullptr, grid, runs, roff);
+    D.covered = D.ml ? make_runs(P.voff, nullptr, grid, runs, roff, 16, ML_SEG) : make_runs(P.voff, nullptr, grid, runs, roff);
     D.nruns = (int32_t)runs.size();
     if (D.sched == 4)
         for (int b = 0; b < grid; ++b)
@@ -1717,7 +1606,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
                 D.sched = 1;   // more pieces per block than the kernel's run table: static schedule
                 break;
             }
-    D.runs_cap = std::max<int64_t>(D.nruns, (int64_t)grid + P.K);   // room for the rebuilt runs
+    // room for the rebuilt runs (and, with the preconditioner, for runs cut at ML_SEG rows)
+    D.runs_cap = std::max<int64_t>(D.nruns, (int64_t)grid + P.K) + (D.ml ? ceil_div(n, ML_SEG) + grid + P.K : 0);
     D.runs.alloc(std::max<int64_t>(1, D.runs_cap), s);
     D.run_off.alloc(grid + 1, s);
     // runs of a piece are consecutive (blocks and their runs follow the rows)
@@ -1802,7 +1692,8 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     auto set_runs = [&](const std::vector<uint8_t>* active) {
         std::vector<DfRun> runs;
         std::vector<int32_t> roff;
-        D.covered = make_runs(P.voff, active, D.grid, runs, roff);
+        D.covered = D.ml ? make_runs(P.voff, active, D.grid, runs, roff, 16, ML_SEG)
+                         : make_runs(P.voff, active, D.grid, runs, roff);
         if ((int64_t)runs.size() > D.runs_cap) fail(PGCP_E_CUDA, "rebuilt PCG runs exceed their buffer");
         D.nruns = (int32_t)runs.size();
         PGCP_CUDA(cudaMemcpyAsync(D.runs.p, runs.data(), runs.size() * sizeof(DfRun), cudaMemcpyHostToDevice, s));
@@ -1817,10 +1708,12 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     if (D.covered != D.n) set_runs(nullptr);
     if (D.f32) prep_typed<ArithF32>(ctx, P, D, r64);
     else prep_typed<ArithDF>(ctx, P, D, r64);
+    if (D.ml) D.ml_M.zero();   // both parities of the preconditioner's moments
     auto launch = [&](int k0, int cap) {
         EventPair ev;   // brackets the persistent kernel only
         PGCP_CUDA(cudaEventRecord(ev.a, s));
-        if (D.f32) launch_typed<ArithF32>(ctx, P, D, k0, cap);
+        if (D.ml) ml_launch(ctx, P, D, k0, cap);
+        else if (D.f32) launch_typed<ArithF32>(ctx, P, D, k0, cap);
         else launch_typed<ArithDF>(ctx, P, D, k0, cap);
         PGCP_CUDA(cudaEventRecord(ev.b, s));
         int k_end = 0;
@@ -1876,9 +1769,16 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     // read and written) -> 4 + 19T; per stored entry column 4 + value T.  At
     // seven entries a row that is 240 B (double-float) and 136 B (FP32).
     // Touched bytes (what this kernel's schedule streams): per row 8 + 22T.
+    // With the multilevel preconditioner: two more vector streams (z written,
+    // z read), the vertex position 12 and the preconditioner's block tables.
     const double T = D.f32 ? 4.0 : 8.0;
-    P.stats.pcg_bytes += (double)w[0] * (4.0 + 19.0 * T) + (double)w[1] * (4.0 + T);
-    P.stats.pcg_bytes_touched += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
+    if (D.ml) {
+        P.stats.pcg_bytes += (double)w[0] * (4.0 + 23.0 * T + 12.0 + D.ml_row_bytes) + (double)w[1] * (4.0 + T);
+        P.stats.pcg_bytes_touched += (double)w[0] * (8.0 + 26.0 * T + 24.0 + D.ml_row_bytes) + (double)w[1] * (4.0 + T);
+    } else {
+        P.stats.pcg_bytes += (double)w[0] * (4.0 + 19.0 * T) + (double)w[1] * (4.0 + T);
+        P.stats.pcg_bytes_touched += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
+    }
     return it;
 }
 

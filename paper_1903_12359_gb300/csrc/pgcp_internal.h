@@ -274,8 +274,37 @@ struct DfSystem {
     int det = 0;
     DBuf<int32_t> prun, RDONE;
     DBuf<double> PRR, PRD, PPQ, CRR;
+    // multilevel preconditioner (pcg_ml.cu): nested row blocks of every piece,
+    // all levels concatenated; block b of level l is entry ml_lofs[l] + b
+    int ml = 0, ml_nl = 0, ml_per_sm = 0;
+    std::vector<int32_t> ml_bofs_h;     // [ML_MAXL][K+1] first block of each piece per level
+    int64_t ml_lofs[16] = {0};          // [ML_MAXL+1]
+    int64_t ml_tofs[16] = {0};          // [ML_MAXL+1] first packed-factor entry of each level
+    double ml_row_bytes = 0.0;          // preconditioner table bytes per row and iteration
+    DBuf<int32_t> ml_bofs, ml_ltop, ml_pvoff;
+    DBuf<float> ml_xr;                  // [3n] vertex positions in their piece's frame
+    DBuf<float4> ml_geo;                // per block: centroid, 1 / RMS radius
+    DBuf<float> ml_T;                   // packed upper-triangular factors
+    DBuf<uint8_t> ml_sep;               // per block: 1 when x and y decouple (T = diag(Tx, Tx))
+    DBuf<float> ml_M;                   // [2][blocks][20] residual moments (iteration parity)
+    DBuf<unsigned char> z;              // preconditioned residual (same layout as r)
 };
+// Multilevel preconditioner constants: a block of level l holds 16 * 4^l rows.
+constexpr int ML_MAXL = 10;
+constexpr int ML_NM = 20;               // moments per block: 10 monomials x (x, y)
+constexpr int ML_SEG = 4096;            // longest run of the preconditioned kernel (rows)
 void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D);
+// Row runs of the persistent grid over the active pieces (all when active is
+// null): `grid` near-equal ranges, cut at piece boundaries; with align > 1 every
+// cut inside a piece falls on a multiple of `align` rows from the piece's first
+// row, and with maxlen > 0 no run is longer than maxlen.  Returns rows covered.
+int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* active, int grid,
+                  std::vector<DfRun>& runs, std::vector<int32_t>& roff, int align = 1, int maxlen = 0);
+// Multilevel preconditioner of a double-float DNCP system (pcg_ml.cu): block
+// tables and factors, after df_build has made the scaled matrix.
+void ml_build(pgcp_ctx* ctx, Part& P, const uint8_t* fixed, DfSystem& D);
+// One persistent launch of the preconditioned kernel over iterations k0 .. cap-1.
+void ml_launch(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap);
 // One inner solve of A d = r64 (thresholds on the unscaled <r, r> per piece
 // and coordinate); adds d to x; returns the iterations run.
 int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x, const std::vector<double>& thr,
