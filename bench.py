@@ -4,7 +4,7 @@
 A step is one pass of the whole path over one mesh already resident in device
 memory: partition -> cotangent assembly + DNCP (batched PCG) -> partial welds
 + disk map -> final Laplace solve (FP32 PCG inside FP64 refinement, relative
-residual <= 1e-10 per piece and coordinate) -> gathered disk coordinates in
+residual <= 1e-12 per piece and coordinate) -> gathered disk coordinates in
 device memory.  value = vertices / s over K timed steps (CUDA events on the
 library's stream, barrier + synchronize on both sides, max over ranks; L2 is
 flushed with a 256 MB write before every step).  e2e repeats the measurement
@@ -40,6 +40,10 @@ sys.path.insert(0, ROOT)
 METRIC = "PGCP end-to-end vertices/s at 1M verts (resid≤1e-10), learned+batched vs plain"
 WORKLOAD = ("1M-vertex Delaunay height field (sum of 8 Gaussians) over the unit disk, "
             "cut along a 4x2 grid of straight vertex rows into 8 pieces; disk map")
+# stopping rule: relative residual <= 1e-12 per piece and coordinate (the metric's
+# <= 1e-10 holds a fortiori; at 1e-10 the max angle distortion of the 1M mesh
+# differs from the oracle's by about 2e-5 degrees, above the 1e-6 bar)
+TOL = 1e-12
 SAMPLE_N = 250_000        # reference-arm step: a bounded sample of the workload
 
 
@@ -130,7 +134,7 @@ def run_batch(api, torch, ms, steps: int, warmup: int) -> dict:
     dev = [(torch.as_tensor(m.V, device="cuda"), torch.as_tensor(m.F, device="cuda", dtype=torch.int32),
             torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)) for m in ms]
     nv = sum(m.nv for m in ms)
-    ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, local_precision=api.DF64_REFINED)
+    ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=TOL, local_precision=api.DF64_REFINED)
     rows = []
     for i in range(warmup + steps):
         torch.cuda.synchronize()
@@ -311,7 +315,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def make_ctx(warm):
-        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, warm_start=warm,
+        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=TOL, warm_start=warm,
                            local_precision=args.local_precision)
 
     def step(ctx):
@@ -454,7 +458,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nv": m.nv, "nf": m.nf, "pieces": s0["K"], "variant": "disk",
-                       "tol": 1e-10, "precision": "final solve: FP32 PCG in FP64 refinement; DNCP: " +
+                       "tol": TOL, "tol_note": "the metric's residual <= 1e-10 holds; the bench stops at 1e-12, where the result matches the oracle within the parity bars (coordinates 1e-8, |d| statistics 1e-6 degrees)", "precision": "final solve: FP32 PCG in FP64 refinement; DNCP: " +
                        ("double-float PCG in FP64 refinement" if df else "FP64 PCG"), "warm_start": "weld map",
                        "l2": "flushed before every step (256 MB write)",
                        "plain_cold_start_value": value_cold,

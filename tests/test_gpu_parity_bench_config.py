@@ -2,9 +2,10 @@
 (seed 0, 4 x 2 cut grid, 8 pieces) with the bench's solver options, against
 the FP64 oracle run on the same mesh.
 
-Two stopping tolerances (relative residual per piece and coordinate, the
+Three stopping tolerances (relative residual per piece and coordinate, the
 reading of Section 4.5 "solve the Laplace equation"):
-- 1e-10, the throughput stopping rule;
+- 1e-10, the residual the headline metric names;
+- 1e-12, the bench's stopping rule;
 - 1e-13, the parity setting of the smaller parity cases.
 
 For each, the DNCP map of every piece (Section 4.2), the final disk map and the
@@ -12,10 +13,13 @@ angle-distortion statistics (Section 5) are compared element by element, and
 the measured maximum errors are printed (and appended as one JSON line to the
 file named by PGCP_PARITY_REPORT, when set).
 
-Bars: a relative residual of 1e-10 bounds the coordinate error only through
-the conditioning of the piece systems, so the bench rule is held to the
-mixed-precision bar of 1e-8 on the final map with 1e-6 degrees on the |d|
-statistics; at 1e-13 the DNCP map must also agree to 1e-9.
+Bars: a relative residual bounds the coordinate error only through the
+conditioning of the piece systems.  At 1e-10 the final map meets the
+mixed-precision bar of 1e-8 and the mean, sd, median and IQR of |d| agree to
+1e-6 degrees, but the max of |d| -- one corner of a triangle about 2e-3 wide --
+moves by about 2e-5 degrees; that is why the bench stops at 1e-12, where every
+statistic must agree to 1e-6 degrees.  At 1e-13 the DNCP map must also agree
+to 1e-9.
 """
 import json
 import os
@@ -50,7 +54,7 @@ def bench_case():
     return m, ref, angle_distortion(m.V, m.F, ref.out)
 
 
-@pytest.mark.parametrize("tol", [1e-10, 1e-13])
+@pytest.mark.parametrize("tol", [1e-10, 1e-12, 1e-13])
 def test_bench_mesh_matches_oracle(api, bench_case, tol):
     m, ref, ad = bench_case
     ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=tol, local_precision=api.DF64_REFINED)
@@ -77,7 +81,8 @@ def test_bench_mesh_matches_oracle(api, bench_case, tol):
         with open(os.environ["PGCP_PARITY_REPORT"], "a") as f:
             f.write(json.dumps(report) + "\n")
     assert final_err < 1e-8, report
-    assert max(d_err.values()) < 1e-6, report
+    assert max(d_err[k] for k in ("mean", "sd", "median", "iqr")) < 1e-6, report
+    assert d_err["max"] < (1e-4 if tol > 1e-12 else 1e-6), report
     assert met["flips"] == 0
     if tol <= 1e-13:
         assert dncp_err < 1e-9, report
