@@ -13,21 +13,27 @@ Readings (the same in the CUDA library):
 * mu of a face is that of the affine map from the surface triangle, laid flat
   in its own orthonormal frame (p0 at 0, p1 on +x), to the parameter triangle:
   mu = f_zbar / f_z.  The inverse map has the same |mu|, so the check of
-  Algorithm 3 on mu of the inverse is the check |mu| >= 1 - 1e-6 here.
-* The composition phi_2 o phi is built directly from its Beltrami coefficient
-  nu: nu = mu_phi on faces that do not fold (the composition leaves the map
-  unchanged there), and nu = (1 - CAP) mu_phi / |mu_phi| on faces that fold
-  (the composition formula with phi_2 undoing the part of mu beyond the unit
-  disk: the argument of the distortion is kept, its modulus brought below 1).
-* The map with coefficient nu and the piece's welded boundary values is the
-  solution of the linear Beltrami solver: div(A_nu grad u) = 0 and
+  Algorithm 3 on mu of the inverse is the check |mu| >= 1 - 1e-6 (or a signed
+  area <= 0) here.
+* A map with Beltrami coefficient nu and the piece's welded boundary values is
+  the solution of the linear Beltrami solver: div(A_nu grad u) = 0 and
   div(A_nu grad v) = 0 for phi = u + i v, with
       A_nu = [[(rho-1)^2 + tau^2, -2 tau], [-2 tau, (rho+1)^2 + tau^2]] / (1 - |nu|^2),
   nu = rho + i tau, discretised with linear elements on the surface
   triangles (each in its own flat frame).  With nu = 0 the element matrices
   are the cotangent stiffness matrices; with nu = mu_phi on every face the
-  solution is phi itself (exact for piecewise linear maps), so only pieces
-  that fold change.
+  solution is phi itself (exact for piecewise linear maps), so a composition
+  changes the map only where nu differs from mu_phi.
+* The composition of Algorithm 3 (the paper gives no discrete recipe) runs in
+  rounds t = 1 .. ROUNDS on a piece that folds.  The fold region is the folded
+  faces grown by t rings of faces that share a vertex; the composition's
+  coefficient nu is mu_phi outside the region and mu_phi with its modulus
+  capped at KAPPA inside it (the composition formula with phi_2 removing the
+  excess distortion, Section 3.5); the new map is the solver's solution for nu
+  with the boundary kept.  The rounds stop as soon as no face folds.
+  KAPPA = 0.7: a cap near 1 leaves dragged vertices in place, a cap near 0
+  forbids the dilatation a fold next to a concave boundary needs; 0.7 fixes
+  both kinds in the pinned cases.
 """
 from __future__ import annotations
 
@@ -36,7 +42,8 @@ from scipy.sparse import coo_matrix
 from scipy.sparse.linalg import spsolve
 
 FOLD_THRESH = 1e-6   # a face folds when |mu| >= 1 - FOLD_THRESH (or its signed area <= 0)
-CAP = 0.05           # folded faces get |nu| = 1 - CAP
+KAPPA = 0.7          # cap of |nu| inside the fold region
+ROUNDS = 16          # compositions at most
 
 
 def face_frames(V: np.ndarray, F: np.ndarray):
@@ -74,11 +81,22 @@ def folded(V: np.ndarray, F: np.ndarray, w: np.ndarray) -> np.ndarray:
     return (signed_area(F, w) <= 0.0) | (np.abs(beltrami(V, F, w)) >= 1.0 - FOLD_THRESH)
 
 
-def target_coefficient(mu: np.ndarray, bad: np.ndarray) -> np.ndarray:
-    """nu: mu where the face does not fold, (1 - CAP) mu / |mu| where it does."""
+def fold_region(F: np.ndarray, n: int, bad: np.ndarray, rings: int) -> np.ndarray:
+    """The faces within `rings` rings (faces sharing a vertex) of the bad faces."""
+    reg = bad.copy()
+    for _ in range(rings):
+        mark = np.zeros(n, dtype=bool)
+        mark[F[reg].ravel()] = True
+        reg = mark[F].any(axis=1)
+    return reg
+
+
+def target_coefficient(mu: np.ndarray, region: np.ndarray) -> np.ndarray:
+    """nu: mu outside the region; inside, mu with its modulus capped at KAPPA."""
     nu = mu.copy()
-    a = np.abs(mu[bad])
-    nu[bad] = np.where(a > 0.0, (1.0 - CAP) * mu[bad] / np.where(a > 0.0, a, 1.0), 0.0)
+    a = np.abs(mu)
+    cap = region & (a > KAPPA)
+    nu[cap] = KAPPA * mu[cap] / a[cap]
     return nu
 
 
@@ -132,26 +150,33 @@ def lbs_solve(V: np.ndarray, F: np.ndarray, loop: np.ndarray, nu: np.ndarray, wb
 
 def fix_piece(V: np.ndarray, F: np.ndarray, loop: np.ndarray, w: np.ndarray):
     """Algorithm 3's fold check and fix on one piece (local ids).  Returns the
-    new map and the number of faces that folded before."""
-    bad = folded(V, F, w)
-    if not bad.any():
-        return w.copy(), 0
-    nu = target_coefficient(beltrami(V, F, w), bad)
-    return lbs_solve(V, F, loop, nu, w[loop]), int(bad.sum())
+    new map, the number of faces that folded before, the compositions made and
+    the faces that still fold after them."""
+    cur = w.copy()
+    bad = folded(V, F, cur)
+    before = int(bad.sum())
+    t = 0
+    while bad.any() and t < ROUNDS:
+        t += 1
+        nu = target_coefficient(beltrami(V, F, cur), fold_region(F, V.shape[0], bad, t))
+        cur = lbs_solve(V, F, loop, nu, cur[loop])
+        bad = folded(V, F, cur)
+    return cur, before, t, int(bad.sum())
 
 
 def fix_folds(V: np.ndarray, F: np.ndarray, part, U: np.ndarray):
     """The fix on every piece of a planar result U [nv, 2] (free or disk
     variant), boundary values kept; the gather takes the lowest-label piece's
-    copy.  Returns (new U, folded faces per piece)."""
+    copy.  Returns (new U, per piece (folded before, compositions, folded
+    after))."""
     out = np.full(U.shape, np.nan)
     counts = []
     w_all = U[:, 0] + 1j * U[:, 1]
     for i in range(part.K):
         g = part.verts[i]
         loop = np.searchsorted(g, part.loops[i])
-        w, nb = fix_piece(V[g], part.local_F[i], loop, w_all[g])
-        counts.append(nb)
+        w, nb, t, na = fix_piece(V[g], part.local_F[i], loop, w_all[g])
+        counts.append((nb, t, na))
         have = ~np.isnan(out[g, 0])
         out[g[~have], 0] = w.real[~have]
         out[g[~have], 1] = w.imag[~have]
