@@ -280,6 +280,35 @@ typedef struct {
  */
 pgcp_status pgcp_area_mobius(pgcp_ctx* ctx, const pgcp_part* part, double* U, int32_t variant, pgcp_area_result* out);
 
+/* Result of the fold-over fix (host struct). */
+typedef struct {
+    int64_t folded_before;   /* faces that folded in the input map */
+    int64_t folded_after;    /* faces that still fold after the fix (0 unless rounds ran out) */
+    int32_t rounds;          /* compositions made (0 when nothing folded) */
+    int32_t pieces_fixed;    /* pieces that folded */
+} pgcp_fold_report;
+
+/*
+ * Fold-over fix (Section 4.5 and the last step of Algorithm 3; Beltrami
+ * coefficient and composition formula, Section 3.5).  A piece's map folds
+ * where a face's Beltrami coefficient mu (of the affine map from the surface
+ * triangle, in its own flat frame, to the parameter triangle) has |mu| >=
+ * 1 - 1e-6, or its signed area is <= 0.  Every piece that folds is composed
+ * with a quasi-conformal map, in rounds t = 1, 2, ... (at most 16): the
+ * faces within t rings (faces sharing a vertex) of the folded faces have their
+ * coefficient capped at modulus 0.7, every other face keeps it, and the map
+ * with those coefficients and the piece's boundary values is solved by the
+ * linear Beltrami solver (div(A_nu grad u) = 0 for both coordinates, linear
+ * elements on the surface triangles; A_nu = I gives the cotangent Laplacian),
+ * until no face folds.  Pieces that do not fold are left bit for bit.
+ *   U: device [nv_total*2], the planar map of the part's mesh (free or disk
+ *   parts; closed parts return PGCP_E_ARG), updated in place; every copy of a
+ *   vertex takes U of that vertex, and the gather takes the lowest-label copy.
+ *   rep: host, may be NULL.
+ * The solves use the context's final-solve precision and tolerance.
+ */
+pgcp_status pgcp_fix_folds(pgcp_ctx* ctx, pgcp_part* part, double* U, pgcp_fold_report* rep);
+
 /*
  * pgcp_metrics without any device allocation.  Library plumbing: the paper has
  * no counterpart.  For callers that must not allocate device memory, because

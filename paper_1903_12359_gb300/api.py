@@ -65,6 +65,14 @@ class Distortion(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class FoldReport(C.Structure):
+    _fields_ = [("folded_before", C.c_int64), ("folded_after", C.c_int64), ("rounds", C.c_int32),
+                ("pieces_fixed", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class AreaResult(C.Structure):
     _fields_ = [("param", C.c_double * 3), ("before", C.c_double), ("after", C.c_double),
                 ("evals", C.c_int32), ("status", C.c_int32)]
@@ -105,6 +113,7 @@ SIGNATURES = {
     "pgcp_metrics_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(Distortion)]),
     "pgcp_area_distortion": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double)]),
     "pgcp_area_mobius": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(AreaResult)]),
+    "pgcp_fix_folds": (C.c_int, [_P, _P, _P, C.POINTER(FoldReport)]),
     "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
                            C.POINTER(Stats)]),
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
@@ -443,6 +452,15 @@ class Part:
         out = (AreaResult * n)()
         self.ctx.check(load().pgcp_area_mobius(self.ctx.h, self.h, _ptr(U), int(variant), out))
         return [r.as_dict() for r in out]
+
+    def fix_folds(self, U):
+        """pgcp_fix_folds: the fold-over fix (Section 4.5, Algorithm 3) on the
+        planar map U in place (contiguous float64 CUDA tensor [nv, 2]); returns
+        the report dict."""
+        check_coords(U, self.nv, self.closed, self.ctx.device, inplace=True)
+        rep = FoldReport()
+        self.ctx.check(load().pgcp_fix_folds(self.ctx.h, self.h, _ptr(U), C.byref(rep)))
+        return rep.as_dict()
 
     def metrics_noalloc(self, U):
         """pgcp_metrics_noalloc: the same statistics with no device allocation,

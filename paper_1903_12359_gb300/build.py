@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpgcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["primitives.cu", "partition.cu", "schedule.cu", "assemble.cu", "pcg.cu", "pcg_df.cu", "pcg_ml.cu", "weld.cu",
-           "solve.cu", "metrics.cu", "area.cu", "gemm_tc.cu", "mpnn.cu", "api.cu"]
+           "solve.cu", "qcfix.cu", "metrics.cu", "area.cu", "gemm_tc.cu", "mpnn.cu", "api.cu"]
 NO_FMA = {"weld.cu"}
 
 

@@ -414,6 +414,21 @@ pgcp_status pgcp_area_mobius(pgcp_ctx* ctx, const pgcp_part* part, double* U, in
     });
 }
 
+pgcp_status pgcp_fix_folds(pgcp_ctx* ctx, pgcp_part* part, double* U, pgcp_fold_report* rep) {
+    return guard(ctx, [&] {
+        if (!ctx || !part || !U) fail(PGCP_E_ARG, "null argument");
+        Part& P = part->p;
+        if (P.closed) fail(PGCP_E_ARG, "the fold fix takes planar maps (free or disk parts)");
+        if (!P.row_ptr.p) {
+            assemble_laplacian(ctx, P);
+            P.stats.nnz = P.nnz;
+        }
+        pgcp_fold_report r{};
+        fix_folds(ctx, P, U, &r);
+        if (rep) *rep = r;
+    });
+}
+
 pgcp_status pgcp_metrics_noalloc(pgcp_ctx* ctx, const pgcp_part* part, const double* U, pgcp_distortion* met) {
     return guard(ctx, [&] {
         if (!ctx || !part || !U || !met) fail(PGCP_E_ARG, "null argument");
@@ -556,7 +571,8 @@ pgcp_status pgcp_autotune(pgcp_ctx* ctx, pgcp_part* part, int32_t probe_iters, p
             // the multilevel preconditioner runs on the static schedule only, and the
             // probes compare time per iteration, which is meaningless across
             // preconditioners: the static schedule is the one candidate
-            cands.push_back(Cand{saved.pcg_blocks_per_sm, 1, saved.spmv_lanes, saved.block_rows_log2});
+            cands.push_back(Cand{saved.pcg_blocks_per_sm ? saved.pcg_blocks_per_sm : 4, 1, saved.spmv_lanes,
+                                 saved.block_rows_log2});
         } else {
             // deterministic mode runs the static schedule only
             for (int sched : {1, 2, 3, 4})

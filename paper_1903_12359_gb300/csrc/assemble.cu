@@ -214,6 +214,25 @@ void assemble_laplacian(pgcp_ctx* ctx, Part& P) {
     uint32_t e = read_errors(ctx);
     if (e & DE_DEGENERATE) fail(PGCP_E_DEGENERATE, "zero-area face");
     if (e & DE_VALENCE) fail(PGCP_E_ARG, "a vertex has more than 64 incident faces in one piece");
+    // the incidence stays with the part: other element matrices on the same
+    // pattern (the fold fix's Beltrami solver) are assembled from it
+    P.inc_off = std::move(off);
+    P.inc = std::move(inc);
+    P.rp64 = std::move(rp64);
+}
+
+void assemble_values(pgcp_ctx* ctx, Part& P, const double* fw, double* val64, float* val32, double* diag64) {
+    cudaStream_t s = ctx->stream;
+    const int64_t Nc = P.Nc;
+    if (!P.inc.p || !P.inc_off.p || !P.rp64.p) fail(PGCP_E_ARG, "the part's Laplacian is not assembled");
+    DBuf<int32_t> rp, cl;   // the pattern is rewritten identically; kept apart from the part's
+    rp.alloc(Nc + 1, s);
+    cl.alloc(std::max<int64_t>(P.nnz, 1), s);
+    ctx->err.zero();
+    { k_row_fill<<<nblk(Nc, 128), 128, 0, s>>>(P.cF.p, P.inc_off.p, P.inc.p, fw, Nc, P.rp64.p, rp.p, cl.p, val64,
+                                             val32, diag64, ctx->err.p); ::pgcp::note_launch(); }
+    PGCP_CUDA(cudaGetLastError());
+    if (read_errors(ctx) & DE_VALENCE) fail(PGCP_E_ARG, "a vertex has more than 64 incident faces in one piece");
 }
 
 }  // namespace pgcp

@@ -83,37 +83,41 @@ __host__ __device__ __forceinline__ void mono10(R x, R y, R z, R* m) {
     m[8] = y * z;
     m[9] = z * z;
 }
-__constant__ int PA[6] = {0, 0, 1, 0, 1, 2};   // the two factors of quadratic monomial 4 + q
-__constant__ int PB[6] = {0, 1, 1, 2, 2, 2};
+// the two factors (a, b) of quadratic monomial 4 + q: xx xy yy xz yz zz
+__host__ __device__ __forceinline__ int qa(int q) { return (q == 2 || q == 4) ? 1 : (q == 5 ? 2 : 0); }
+__host__ __device__ __forceinline__ int qb(int q) { return q == 0 ? 0 : (q <= 2 ? 1 : 2); }
 
-// Moments of the same rows in the parent frame: xi_p = s xi_c + t.
-__device__ __forceinline__ void mom_to_parent(const float* mc, float s, const float* t, float* mp) {
-    mp[0] += mc[0];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) mp[1 + a] += s * mc[1 + a] + t[a] * mc[0];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const int a = PA[q], b = PB[q];
-        mp[4 + q] += s * s * mc[4 + q] + s * t[b] * mc[1 + a] + s * t[a] * mc[1 + b] + t[a] * t[b] * mc[0];
-    }
+// Moment k (0..9) of a child's rows in the parent frame, xi_p = s xi_c + t,
+// from the child's ten moments mc.
+__device__ __forceinline__ float mom_out(int k, const float* mc, float s, const float* t) {
+    const float m0 = mc[0];
+    if (k == 0) return m0;
+    if (k < 4) return s * mc[k] + t[k - 1] * m0;
+    const int q = k - 4, a = qa(q), b = qb(q);
+    return s * s * mc[k] + s * t[b] * mc[1 + a] + s * t[a] * mc[1 + b] + t[a] * t[b] * m0;
 }
-// The transpose: coefficients of a parent-frame polynomial re-expanded in the
-// child frame and added to cc.
-__device__ __forceinline__ void coef_to_child(const float* cp, float s, const float* t, float* cc) {
-    cc[0] += cp[0];
+
+// The transpose: coefficient k (0..9) in the child frame of the parent-frame
+// polynomial with coefficients cp.
+__device__ __forceinline__ float coef_out(int k, const float* cp, float s, const float* t) {
+    if (k >= 4) return s * s * cp[k];
+    float v = 0.f;
+    if (k == 0) {
+        v = cp[0];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        cc[1 + a] += s * cp[1 + a];
-        cc[0] += t[a] * cp[1 + a];
+        for (int a = 0; a < 3; ++a) v += t[a] * cp[1 + a];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += t[qa(q)] * t[qb(q)] * cp[4 + q];
+        return v;
     }
+    const int a = k - 1;
+    v = s * cp[k];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        const int a = PA[q], b = PB[q];
-        cc[4 + q] += s * s * cp[4 + q];
-        cc[1 + a] += s * t[b] * cp[4 + q];
-        cc[1 + b] += s * t[a] * cp[4 + q];
-        cc[0] += t[a] * t[b] * cp[4 + q];
+        if (qa(q) == a) v += s * t[qb(q)] * cp[4 + q];
+        if (qb(q) == a) v += s * t[qa(q)] * cp[4 + q];
     }
+    return v;
 }
 
 struct MlArgs {
@@ -154,43 +158,58 @@ __device__ __forceinline__ bool done_of(const double* RD, const double* THR, int
     return __ldcg(RD + 2 * s + c) <= THR[2 * s + c];
 }
 
-// c = T (T^T m) for one block (m, c: [2 nf1], x part then y part).
-__device__ __forceinline__ void block_coef(const float* __restrict__ T, bool sep, int nf1, const float* m, float* c) {
-    float u[20];
-    if (sep) {
-        for (int h = 0; h < 2; ++h) {
-            const float* mh = m + h * nf1;
-            for (int j = 0; j < nf1; ++j) {
-                float a = 0.f;
-                for (int i = 0; i <= j; ++i) a = fmaf(__ldg(T + ut(i, j, nf1)), mh[i], a);
-                u[j] = a;
-            }
-            for (int i = 0; i < nf1; ++i) {
-                float a = 0.f;
-                for (int j = i; j < nf1; ++j) a = fmaf(__ldg(T + ut(i, j, nf1)), u[j], a);
-                c[h * nf1 + i] = a;
-            }
-        }
-        return;
-    }
-    const int nf = 2 * nf1;
-    for (int j = 0; j < nf; ++j) {
+// c = T (T^T m) for a packed upper-triangular N x N factor T (compile-time
+// size: every load independent and unrolled).
+template <int N>
+__device__ __forceinline__ void tri_coef(const float* __restrict__ T, const float* m, float* c) {
+    float t[N * (N + 1) / 2];
+#pragma unroll
+    for (int e = 0; e < N * (N + 1) / 2; ++e) t[e] = __ldg(T + e);
+    float u[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
         float a = 0.f;
-        for (int i = 0; i <= j; ++i) a = fmaf(__ldg(T + ut(i, j, nf)), m[i], a);
+#pragma unroll
+        for (int i = 0; i <= j; ++i) a = fmaf(t[ut(i, j, N)], m[i], a);
         u[j] = a;
     }
-    for (int i = 0; i < nf; ++i) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
         float a = 0.f;
-        for (int j = i; j < nf; ++j) a = fmaf(__ldg(T + ut(i, j, nf)), u[j], a);
+#pragma unroll
+        for (int j = i; j < N; ++j) a = fmaf(t[ut(i, j, N)], u[j], a);
         c[i] = a;
     }
 }
 
+// The same for one coarse block by a warp (N = 10 separable, applied to x and
+// y, or N = 20): lane L holds m_L on entry and c_L on return (L < 20).
+__device__ __forceinline__ float warp_coef(const float* __restrict__ T, bool sep, float mL) {
+    const int lane = threadIdx.x & 31;
+    const int n = sep ? 10 : 20;
+    const int h = sep ? (lane >= 10 ? 10 : 0) : 0;   // first lane of this lane's system
+    const int i = lane - h;                          // output index in the system
+    float u = 0.f;
+#pragma unroll
+    for (int k = 0; k < 20; ++k) {   // u_i = sum_{k <= i} T_ki m_k
+        const float mk = __shfl_sync(0xffffffffu, mL, (h + k) & 31);
+        if (k <= i && k < n && lane < 20) u = fmaf(__ldg(T + ut(k, i, n)), mk, u);
+    }
+    float c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 20; ++k) {   // c_i = sum_{k >= i} T_ik u_k
+        const float uk = __shfl_sync(0xffffffffu, u, (h + k) & 31);
+        if (k >= i && k < n && lane < 20) c = fmaf(__ldg(T + ut(i, k, n)), uk, c);
+    }
+    return c;
+}
+
 // Restriction for one run: after the level-0 moments of the run's rows are
 // stored (one half-warp per 16-row block), the coarser levels' partial moments
-// from this run's rows, summed into M: a block inside the run is stored, a
-// block shared with other runs is added atomically (its slot was cleared by
-// the run holding its first row).  smem: two ping-pong buffers in buf.
+// from this run's rows, one (block, moment) per thread, summed into M: a block
+// inside the run is stored, a block shared with other runs is added
+// atomically (its slot was cleared by the run holding its first row).
+// smem: two ping-pong buffers in buf.
 __device__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int par) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
@@ -205,36 +224,25 @@ __device__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int p
         const int c0 = lo >> shc, c1 = (hi - 1) >> shc;
         const int64_t gb0 = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s];
         const int64_t gc0 = a.lofs[l - 1] + a.bofs[(l - 1) * (a.nseg + 1) + s];
-        for (int j = threadIdx.x; j <= b1 - b0; j += blockDim.x) {
+        for (int task = threadIdx.x; task < (b1 - b0 + 1) * ML_NM; task += blockDim.x) {
+            const int j = task / ML_NM, k = task - j * ML_NM;
+            const int h = k >= 10 ? 10 : 0;
             const int blk = b0 + j;
             const float4 gp = a.geo[gb0 + blk];
-            float acc[ML_NM];
-#pragma unroll
-            for (int f = 0; f < ML_NM; ++f) acc[f] = 0.f;
+            float acc = 0.f;
             const int cl = max(blk * 4, c0), ch = min(blk * 4 + 3, c1);
             for (int c = cl; c <= ch; ++c) {
                 const float4 gc = a.geo[gc0 + c];
                 const float sc = gp.w / gc.w;
                 const float t[3] = {(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w, (gc.z - gp.z) * gp.w};
-                float mc[ML_NM];
-                const float* src = l == 1 ? Mp + (gc0 + c) * ML_NM : prev + (c - c0) * ML_NM;
-#pragma unroll
-                for (int f = 0; f < ML_NM; ++f) mc[f] = src[f];
-                mom_to_parent(mc, sc, t, acc);
-                mom_to_parent(mc + 10, sc, t, acc + 10);
+                const float* src = (l == 1 ? Mp + (gc0 + c) * ML_NM : prev + (c - c0) * ML_NM) + h;
+                acc += mom_out(k - h, src, sc, t);
             }
-            float* dst = cur + j * ML_NM;
-#pragma unroll
-            for (int f = 0; f < ML_NM; ++f) dst[f] = acc[f];
-            float* g = Mp + (gb0 + blk) * ML_NM;
+            cur[j * ML_NM + k] = acc;
+            float* g = Mp + (gb0 + blk) * ML_NM + k;
             const bool inside = (blk << sh) >= lo && min((blk + 1) << sh, nrow) <= hi;
-            if (inside) {
-#pragma unroll
-                for (int f = 0; f < ML_NM; ++f) g[f] = acc[f];
-            } else {
-#pragma unroll
-                for (int f = 0; f < ML_NM; ++f) atomicAdd(g + f, acc[f]);
-            }
+            if (inside) *g = acc;
+            else atomicAdd(g, acc);
         }
         __syncthreads();
         float* t = prev;
@@ -244,54 +252,100 @@ __device__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int p
 }
 
 // Prolongation tables for one run: every level's coefficients c = T T^T m on
-// the blocks the run touches, re-expanded top-down into the level-0 frames;
-// each level-0 slot ends with the combined quadratic (20 values) and the
-// block's frame (4 values).  Also clears the next parity's moments of the
-// blocks whose first row lies in this run (levels >= 1).
+// the blocks the run touches (level 0 one thread per block, coarser levels one
+// warp per block), then re-expanded top-down into the level-0 frames (one
+// (block, coefficient) per thread); each level-0 slot ends with the combined
+// quadratic (20 values) and the block's frame (4 values).  Also clears the
+// next parity's moments of the blocks whose first row lies in this run
+// (levels >= 1).
 __device__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
     const float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
     float* Mn = a.M + (int64_t)(par ^ 1) * a.mstride * ML_NM;
     const int lo = run.lo - pv, hi = run.hi - pv;
-    for (int l = top; l >= 0; --l) {
-        const int sh = ml_shift(l), nf1 = ml_nf1(l);
-        const int b0 = lo >> sh, b1 = (hi - 1) >> sh;
-        const int64_t gb0 = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s];
-        float* tl = tab + ml_capoff(l) * 24;
-        const float* tp = tab + ml_capoff(l + 1 < ML_MAXL ? l + 1 : l) * 24;
-        const int pb0 = l < top ? lo >> ml_shift(l + 1) : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // level 0: one thread per block
+    {
+        const int b0 = lo >> 4, b1 = (hi - 1) >> 4;
+        const int64_t gb0 = a.lofs[0] + a.bofs[s];
         for (int j = threadIdx.x; j <= b1 - b0; j += blockDim.x) {
-            const int blk = b0 + j;
-            const int64_t gb = gb0 + blk;
-            if (l >= 1 && (blk << sh) >= lo) {   // first row in this run: clear the next parity's slot
-#pragma unroll
-                for (int f = 0; f < ML_NM; ++f) Mn[gb * ML_NM + f] = 0.f;
-            }
-            float m[ML_NM], c[ML_NM];
+            const int64_t gb = gb0 + b0 + j;
             const float* src = Mp + gb * ML_NM;
-            for (int f = 0; f < nf1; ++f) {
+            float m[8], c[8];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
                 m[f] = __ldcg(src + f);
-                m[nf1 + f] = __ldcg(src + 10 + f);
+                m[4 + f] = __ldcg(src + 10 + f);
             }
-            block_coef(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l), a.sep[gb] != 0, nf1, m, c);
-            float* dst = tl + j * 24;
+            const float* T = a.T + a.tofs[0] + (gb - a.lofs[0]) * ml_ts(0);
+            if (a.sep[gb]) {
+                tri_coef<4>(T, m, c);
+                tri_coef<4>(T, m + 4, c + 4);
+            } else {
+                tri_coef<8>(T, m, c);
+            }
+            float* dst = tab + j * 24;
+#pragma unroll
             for (int f = 0; f < 10; ++f) {
-                dst[f] = f < nf1 ? c[f] : 0.f;
-                dst[10 + f] = f < nf1 ? c[nf1 + f] : 0.f;
+                dst[f] = f < 4 ? c[f] : 0.f;
+                dst[10 + f] = f < 4 ? c[4 + f] : 0.f;
             }
             const float4 g = a.geo[gb];
-            if (l < top) {   // add the parent's combined polynomial, re-expanded here
-                const float* pc = tp + ((blk >> 2) - pb0) * 24;
-                const float sc = pc[23] / g.w;
-                const float t[3] = {(g.x - pc[20]) * pc[23], (g.y - pc[21]) * pc[23], (g.z - pc[22]) * pc[23]};
-                coef_to_child(pc, sc, t, dst);
-                coef_to_child(pc + 10, sc, t, dst + 10);
-            }
             dst[20] = g.x;
             dst[21] = g.y;
             dst[22] = g.z;
             dst[23] = g.w;
+        }
+    }
+    // levels 1..top: one warp per block, over all levels at once
+    {
+        int total = 0;
+        for (int l = 1; l <= top; ++l) total += ((hi - 1) >> ml_shift(l)) - (lo >> ml_shift(l)) + 1;
+        for (int w = warp; w < total; w += nwarp) {
+            int l = 1, j = w;
+            while (true) {   // the level and block of work item w
+                const int nbl = ((hi - 1) >> ml_shift(l)) - (lo >> ml_shift(l)) + 1;
+                if (j < nbl) break;
+                j -= nbl;
+                ++l;
+            }
+            const int sh = ml_shift(l);
+            const int blk = (lo >> sh) + j;
+            const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            const float mL = lane < ML_NM ? __ldcg(Mp + gb * ML_NM + lane) : 0.f;
+            const float c = warp_coef(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l), a.sep[gb] != 0, mL);
+            float* dst = tab + (ml_capoff(l) + j) * 24;
+            if (lane < ML_NM) {
+                dst[lane] = c;
+                if ((blk << sh) >= lo) Mn[gb * ML_NM + lane] = 0.f;   // first row here: clear the next parity
+            }
+            if (lane == 0) {
+                const float4 g = a.geo[gb];
+                dst[20] = g.x;
+                dst[21] = g.y;
+                dst[22] = g.z;
+                dst[23] = g.w;
+            }
+        }
+    }
+    __syncthreads();
+    // top-down: add the parent's combined polynomial, re-expanded in the child frame
+    for (int l = top - 1; l >= 0; --l) {
+        const int sh = ml_shift(l);
+        const int b0 = lo >> sh, b1 = (hi - 1) >> sh;
+        const int pb0 = lo >> ml_shift(l + 1);
+        float* tl = tab + ml_capoff(l) * 24;
+        const float* tp = tab + ml_capoff(l + 1) * 24;
+        for (int task = threadIdx.x; task < (b1 - b0 + 1) * ML_NM; task += blockDim.x) {
+            const int j = task / ML_NM, k = task - j * ML_NM;
+            const int h = k >= 10 ? 10 : 0;
+            const int blk = b0 + j;
+            float* dst = tl + j * 24;
+            const float* pc = tp + ((blk >> 2) - pb0) * 24;
+            const float sc = pc[23] / dst[23];
+            const float t[3] = {(dst[20] - pc[20]) * pc[23], (dst[21] - pc[21]) * pc[23], (dst[22] - pc[22]) * pc[23]};
+            dst[k] += coef_out(k - h, pc + h, sc, t);
         }
         __syncthreads();
     }

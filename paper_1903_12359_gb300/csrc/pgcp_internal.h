@@ -177,6 +177,8 @@ struct Part {
     DBuf<float> val32;
     DBuf<double> diag64;
     int64_t nnz = 0;
+    DBuf<int64_t> inc_off, rp64;   // corner incidence of every row and the CSR row offsets (int64)
+    DBuf<int32_t> inc;
     // coordinates
     DBuf<double2> local;      // DNCP (local frame)
     DBuf<double2> welded;     // FP64 welded coords (boundary rows exact; interior = weld map)
@@ -313,6 +315,12 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
 void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels_or_null, const int32_t* d_cut, int64_t n_cut);
 void build_schedule(pgcp_ctx* ctx, Part& P);
 void assemble_laplacian(pgcp_ctx* ctx, Part& P);
+// Values of another linear-element matrix on the Laplacian's pattern: fw[3 f + c]
+// is the weight of the edge opposite corner c of face f (piece order); entries
+// -sum of the weights on each edge, diagonal their row sums.
+void assemble_values(pgcp_ctx* ctx, Part& P, const double* fw, double* val64, float* val32, double* diag64);
+// Fold-over fix (qcfix.cu) on a planar map U [nv*2] (device, in and out).
+void fix_folds(pgcp_ctx* ctx, Part& P, double* U, pgcp_fold_report* rep);
 void solve_dncp(pgcp_ctx* ctx, Part& P);
 void run_welds(pgcp_ctx* ctx, Part& P);
 void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out);
