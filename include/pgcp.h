@@ -280,6 +280,32 @@ typedef struct {
  */
 pgcp_status pgcp_area_mobius(pgcp_ctx* ctx, const pgcp_part* part, double* U, int32_t variant, pgcp_area_result* out);
 
+/*
+ * Pieces of one mesh shared among ranks (the paper's parallel scheme, Section
+ * 5.6, with the exchange limited to boundaries: welding reads and writes only
+ * boundary points, Sections 4.3 and 4.5).  Every rank partitions the same mesh
+ * and owns some of its pieces:
+ *  1. pgcp_set_piece_mask, then pgcp_local_param: DNCP maps of the owned
+ *     pieces only (the rows of the other pieces are held at 0);
+ *  2. pgcp_part_get_boundary(which = 0) on every rank; one rank merges the
+ *     owned pieces' loop ranges of all ranks, imports them with
+ *     pgcp_part_set_boundary(which = 0) and runs pgcp_weld (welds and the
+ *     disk map act on boundary points); pgcp_part_get_boundary(which = 1)
+ *     then holds the welded boundary of every piece;
+ *  3. every rank imports that welded boundary (pgcp_part_set_boundary,
+ *     which = 1; interior rows start the final solve at 0) and calls
+ *     pgcp_global_solve: the owned pieces are solved, the output holds NaN
+ *     at the vertices whose lowest-label copy belongs to another rank's piece.
+ *  pgcp_set_piece_mask: own = host uint8 [K] (nonzero: owned), or NULL (all).
+ *  pgcp_part_get_boundary / pgcp_part_set_boundary: device [n_loop * 2],
+ *    (re, im) at every loop position in the order of pgcp_part_get_partition's
+ *    loop_verts; which = 0 the local (DNCP) map, 1 the welded map (open
+ *    parts only).  Importing which = 0 needs pgcp_local_param first.
+ */
+pgcp_status pgcp_set_piece_mask(pgcp_ctx* ctx, pgcp_part* part, const uint8_t* own);
+pgcp_status pgcp_part_get_boundary(pgcp_ctx* ctx, const pgcp_part* part, int32_t which, double* out);
+pgcp_status pgcp_part_set_boundary(pgcp_ctx* ctx, pgcp_part* part, int32_t which, const double* in);
+
 /* Result of the fold-over fix (host struct). */
 typedef struct {
     int64_t folded_before;   /* faces that folded in the input map */

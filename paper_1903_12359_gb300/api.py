@@ -114,6 +114,9 @@ SIGNATURES = {
     "pgcp_area_distortion": (C.c_int, [_P, _P, _P, C.POINTER(C.c_double)]),
     "pgcp_area_mobius": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(AreaResult)]),
     "pgcp_fix_folds": (C.c_int, [_P, _P, _P, C.POINTER(FoldReport)]),
+    "pgcp_set_piece_mask": (C.c_int, [_P, _P, _P]),
+    "pgcp_part_get_boundary": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "pgcp_part_set_boundary": (C.c_int, [_P, _P, C.c_int32, _P]),
     "pgcp_run": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, C.c_int32, _P,
                            C.POINTER(Stats)]),
     "pgcp_selftest_sort": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32]),
@@ -452,6 +455,30 @@ class Part:
         out = (AreaResult * n)()
         self.ctx.check(load().pgcp_area_mobius(self.ctx.h, self.h, _ptr(U), int(variant), out))
         return [r.as_dict() for r in out]
+
+    def set_piece_mask(self, own):
+        """pgcp_set_piece_mask: the pieces this part solves (sequence of K
+        bools), or None for all."""
+        if own is None:
+            self.ctx.check(load().pgcp_set_piece_mask(self.ctx.h, self.h, None))
+            return
+        arr = np.ascontiguousarray(np.asarray(own, dtype=np.uint8))
+        if arr.size != self.info()["K"]:
+            raise ValueError("the mask needs one entry per piece")
+        self.ctx.check(load().pgcp_set_piece_mask(self.ctx.h, self.h, arr.ctypes.data_as(C.c_void_p)))
+
+    def get_boundary(self, which):
+        """pgcp_part_get_boundary: [n_loop, 2] float64 CUDA tensor (0: local, 1: welded)."""
+        out = torch.empty((self.info()["n_loop"], 2), dtype=torch.float64, device="cuda")
+        self.ctx.check(load().pgcp_part_get_boundary(self.ctx.h, self.h, int(which), _ptr(out)))
+        return out
+
+    def set_boundary(self, which, B):
+        """pgcp_part_set_boundary: import [n_loop, 2] boundary coordinates."""
+        B = _dev(B, torch.float64).contiguous()
+        if tuple(B.shape) != (self.info()["n_loop"], 2):
+            raise ValueError("boundary coordinates must be [n_loop, 2]")
+        self.ctx.check(load().pgcp_part_set_boundary(self.ctx.h, self.h, int(which), _ptr(B)))
 
     def fix_folds(self, U):
         """pgcp_fix_folds: the fold-over fix (Section 4.5, Algorithm 3) on the

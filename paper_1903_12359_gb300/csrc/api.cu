@@ -414,6 +414,35 @@ pgcp_status pgcp_area_mobius(pgcp_ctx* ctx, const pgcp_part* part, double* U, in
     });
 }
 
+pgcp_status pgcp_set_piece_mask(pgcp_ctx* ctx, pgcp_part* part, const uint8_t* own) {
+    return guard(ctx, [&] {
+        if (!part) fail(PGCP_E_ARG, "null part");
+        Part& P = part->p;
+        if (!own) {
+            P.own.clear();
+            return;
+        }
+        P.own.assign(own, own + P.K);
+        for (auto& v : P.own) v = v ? 1 : 0;
+    });
+}
+
+pgcp_status pgcp_part_get_boundary(pgcp_ctx* ctx, const pgcp_part* part, int32_t which, double* out) {
+    return guard(ctx, [&] {
+        if (!part || !out) fail(PGCP_E_ARG, "null argument");
+        if (which != 0 && which != 1) fail(PGCP_E_ARG, "which must be 0 (local) or 1 (welded)");
+        part_get_boundary(ctx, part->p, which, out);
+    });
+}
+
+pgcp_status pgcp_part_set_boundary(pgcp_ctx* ctx, pgcp_part* part, int32_t which, const double* in) {
+    return guard(ctx, [&] {
+        if (!part || !in) fail(PGCP_E_ARG, "null argument");
+        if (which != 0 && which != 1) fail(PGCP_E_ARG, "which must be 0 (local) or 1 (welded)");
+        part_set_boundary(ctx, part->p, which, in);
+    });
+}
+
 pgcp_status pgcp_fix_folds(pgcp_ctx* ctx, pgcp_part* part, double* U, pgcp_fold_report* rep) {
     return guard(ctx, [&] {
         if (!ctx || !part || !U) fail(PGCP_E_ARG, "null argument");

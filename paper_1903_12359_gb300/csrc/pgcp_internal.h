@@ -187,6 +187,7 @@ struct Part {
     std::vector<int32_t> mesh_status;   // [meshes] PGCP_OK, or PGCP_E_NUMERIC for a dropped mesh of a batch
     DBuf<uint8_t> d_wchart;
     int32_t have_local = 0, have_weld = 0, have_final = 0;
+    std::vector<uint8_t> own;   // [K] pieces this part solves (empty: all); the rest are another rank's
     pgcp_stats stats{};
 };
 
@@ -324,6 +325,10 @@ void fix_folds(pgcp_ctx* ctx, Part& P, double* U, pgcp_fold_report* rep);
 void solve_dncp(pgcp_ctx* ctx, Part& P);
 void run_welds(pgcp_ctx* ctx, Part& P);
 void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out);
+// Boundary exchange of a sharded run: coordinates at every loop position
+// (which: 0 local map, 1 welded map), out / in device [n_loop * 2].
+void part_get_boundary(pgcp_ctx* ctx, const Part& P, int which, double* out);
+void part_set_boundary(pgcp_ctx* ctx, Part& P, int which, const double* in);
 void compute_metrics(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);
 // Same statistics on a fixed device-side scratch array; no allocation.
 void compute_metrics_noalloc(pgcp_ctx* ctx, const Part& P, const double* U, pgcp_distortion* met);

@@ -32,6 +32,36 @@ __global__ void k_dncp_pins(const int32_t* __restrict__ pin_rows, int32_t K, uin
     x[p1] = make_double2(1.0, 0.0);
 }
 
+// rows of pieces another rank solves: fixed at 0 (their system is empty here)
+__global__ void k_fix_unowned(int64_t n, const int32_t* __restrict__ row_piece, const uint8_t* __restrict__ own,
+                              uint8_t* __restrict__ fixed, double2* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || own[row_piece[i]]) return;
+    fixed[i] = 1;
+    x[i] = make_double2(0.0, 0.0);
+}
+
+__global__ void k_loop_get(int64_t nl, const int32_t* __restrict__ loop_rows, const double2* __restrict__ X,
+                           double* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nl) return;
+    const double2 v = X[loop_rows[j]];
+    out[2 * j] = v.x;
+    out[2 * j + 1] = v.y;
+}
+
+// loop rows take the given values; with zero_inner, every other row is set to 0
+__global__ void k_loop_set(int64_t n, const uint8_t* __restrict__ is_bnd, int zero_inner, double2* __restrict__ X) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && zero_inner && !is_bnd[i]) X[i] = make_double2(0.0, 0.0);
+}
+__global__ void k_loop_put(int64_t nl, const int32_t* __restrict__ loop_rows, const double* __restrict__ in,
+                           double2* __restrict__ X) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nl) return;
+    X[loop_rows[j]] = make_double2(in[2 * j], in[2 * j + 1]);
+}
+
 // translate each piece so its reference vertex is at 0
 __global__ void k_translate(int64_t n, const int32_t* __restrict__ row_piece, const int32_t* __restrict__ ref_rows,
                             const double2* __restrict__ x, double2* __restrict__ out) {
@@ -98,7 +128,7 @@ __global__ void k_gather(int64_t Nc, const int32_t* __restrict__ copy_vert, cons
     coords((int)i, a);
     if (f == (int)i) {
         for (int c = 0; c < dim; ++c) out[(int64_t)dim * v + c] = a[c];
-    } else {
+    } else if (wchart[row_piece[f]] != 2) {   // (a first copy in a skipped piece is written elsewhere)
         coords(f, b);
         double m = 0.0;
         for (int c = 0; c < dim; ++c) m = fmax(m, fabs(a[c] - b[c]));
@@ -130,6 +160,12 @@ void solve_dncp(pgcp_ctx* ctx, Part& P) {
     PGCP_CUDA(cudaMemcpyAsync(refs.p, hr.data(), hr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     { k_dncp_init<<<nblk(n), 256, 0, s>>>(n, fixed.p, x.p); ::pgcp::note_launch(); }
     { k_dncp_pins<<<nblk(P.K), 256, 0, s>>>(pins.p, P.K, fixed.p, x.p); ::pgcp::note_launch(); }
+    DBuf<uint8_t> own;
+    if (!P.own.empty()) {
+        own.alloc(P.K, s);
+        PGCP_CUDA(cudaMemcpyAsync(own.p, P.own.data(), P.K, cudaMemcpyHostToDevice, s));
+        { k_fix_unowned<<<nblk(n), 256, 0, s>>>(n, P.row_piece.p, own.p, fixed.p, x.p); ::pgcp::note_launch(); }
+    }
     PGCP_CUDA(cudaGetLastError());
     SolveResult r = pcg_solve(ctx, P, 1, fixed.p, x.p);
     P.stats.dncp_iters = r.iters;
@@ -187,6 +223,40 @@ void solve_final(pgcp_ctx* ctx, Part& P, double* out, int host_out) {
     P.stats.seam_mismatch = md;
     if (!(r.relres <= ctx->opt.tol))
         fail(PGCP_E_NO_CONVERGENCE, "final Laplace solve reached relative residual " + std::to_string(r.relres));
+}
+
+void part_get_boundary(pgcp_ctx* ctx, const Part& P, int which, double* out) {
+    const DBuf<double2>& X = which == 0 ? P.local : P.welded;
+    if (!(which == 0 ? P.have_local : P.have_weld)) fail(PGCP_E_ARG, which == 0 ? "no local map yet" : "no welded map yet");
+    const int64_t nl = (int64_t)P.loop_rows.size();
+    { k_loop_get<<<nblk(nl), 256, 0, ctx->stream>>>(nl, P.d_loop_rows.p, X.p, out); ::pgcp::note_launch(); }
+    PGCP_CUDA(cudaGetLastError());
+    PGCP_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void part_set_boundary(pgcp_ctx* ctx, Part& P, int which, const double* in) {
+    cudaStream_t s = ctx->stream;
+    const int64_t nl = (int64_t)P.loop_rows.size(), n = P.Nc;
+    if (which == 0) {
+        if (!P.have_local) fail(PGCP_E_ARG, "call pgcp_local_param before importing local boundaries");
+        { k_loop_put<<<nblk(nl), 256, 0, s>>>(nl, P.d_loop_rows.p, in, P.local.p); ::pgcp::note_launch(); }
+    } else {
+        // the welded boundary of every piece; interior rows start at 0 (the
+        // final solve's cold start); pieces this part does not own are skipped
+        if (P.closed) fail(PGCP_E_ARG, "welded boundaries are imported into open parts only");
+        if (!P.welded.p) P.welded.alloc(n, s);
+        { k_loop_set<<<nblk(n), 256, 0, s>>>(n, P.is_bnd.p, 1, P.welded.p); ::pgcp::note_launch(); }
+        { k_loop_put<<<nblk(nl), 256, 0, s>>>(nl, P.d_loop_rows.p, in, P.welded.p); ::pgcp::note_launch(); }
+        P.wchart.assign(P.K, 0);
+        for (int i = 0; i < P.K; ++i)
+            if (!P.own.empty() && !P.own[i]) P.wchart[i] = 2;
+        P.d_wchart.alloc(P.K, s);
+        PGCP_CUDA(cudaMemcpyAsync(P.d_wchart.p, P.wchart.data(), P.K, cudaMemcpyHostToDevice, s));
+        P.mesh_status.assign(P.meshes.size(), PGCP_OK);
+        P.have_weld = 1;
+    }
+    PGCP_CUDA(cudaGetLastError());
+    PGCP_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace pgcp

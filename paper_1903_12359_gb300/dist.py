@@ -56,3 +56,58 @@ def throughput(units_per_rank: float, ms_per_rank: float, device=None) -> float:
     units = sum_over_ranks(units_per_rank, device)
     ms = max_over_ranks(ms_per_rank, device)
     return units / (ms / 1000.0)
+
+
+def sharded_map(ctx, V, F, face_labels):
+    """One mesh's pieces shared among the ranks of the current process group.
+
+    Every rank partitions the mesh and solves the DNCP maps of the pieces the
+    LPT assignment (on face counts) gives it.  The boundary coordinates go up
+    to rank 0 (16 bytes per loop position of an owned piece), which welds them
+    and runs the disk map; the welded boundary comes back down (16 bytes per
+    loop position); every rank then solves the Laplace problems of its pieces.
+    Returns (map [nv, 2] on rank 0, None elsewhere; dict of the bytes each
+    exchange moved).  The library does all the arithmetic; this function only
+    moves arrays between ranks (object collectives, gloo or NCCL).
+    """
+    import numpy as np
+    import torch.distributed as dist
+    ws, rank = dist.get_world_size(), dist.get_rank()
+    part = ctx.partition(V, F, face_labels=face_labels)
+    try:
+        fl, voff, verts, loff, loops = [t.cpu().numpy() for t in part.partition_arrays()]
+        K = voff.size - 1
+        shards = lpt_shard([float(c) for c in np.bincount(fl, minlength=K)], ws)
+        own = np.zeros(K, dtype=bool)
+        own[shards[rank]] = True
+        part.set_piece_mask(own)
+        part.local_param()
+        B = part.get_boundary(0).cpu().numpy()
+        mine = {i: B[loff[i]:loff[i + 1]] for i in shards[rank]}
+        up = [None] * ws if rank == 0 else None
+        dist.gather_object(mine, up, dst=0)
+        W = [None]
+        if rank == 0:
+            full = B.copy()
+            for d in up:
+                for i, b in d.items():
+                    full[loff[i]:loff[i + 1]] = b
+            part.set_boundary(0, full)
+            part.weld()
+            W = [part.get_boundary(1).cpu().numpy()]
+        dist.broadcast_object_list(W, src=0)
+        part.set_boundary(1, W[0])
+        out = part.global_solve().cpu().numpy()
+        outs = [None] * ws if rank == 0 else None
+        dist.gather_object(out, outs, dst=0)
+        moved = {"boundary_up_bytes": int(sum(loff[i + 1] - loff[i] for i in range(K)) * 16),
+                 "boundary_down_bytes": int(W[0].nbytes)}
+        if rank != 0:
+            return None, moved
+        merged = outs[0].copy()
+        for o in outs[1:]:
+            take = ~np.isnan(o[:, 0])
+            merged[take] = o[take]
+        return merged, moved
+    finally:
+        part.free()
