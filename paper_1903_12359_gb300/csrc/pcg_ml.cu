@@ -162,22 +162,19 @@ __device__ __forceinline__ bool done_of(const double* RD, const double* THR, int
 // size: every load independent and unrolled).
 template <int N>
 __device__ __forceinline__ void tri_coef(const float* __restrict__ T, const float* m, float* c) {
-    float t[N * (N + 1) / 2];
-#pragma unroll
-    for (int e = 0; e < N * (N + 1) / 2; ++e) t[e] = __ldg(T + e);
     float u[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         float a = 0.f;
 #pragma unroll
-        for (int i = 0; i <= j; ++i) a = fmaf(t[ut(i, j, N)], m[i], a);
+        for (int i = 0; i <= j; ++i) a = fmaf(__ldg(T + ut(i, j, N)), m[i], a);
         u[j] = a;
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         float a = 0.f;
 #pragma unroll
-        for (int j = i; j < N; ++j) a = fmaf(t[ut(i, j, N)], u[j], a);
+        for (int j = i; j < N; ++j) a = fmaf(__ldg(T + ut(i, j, N)), u[j], a);
         c[i] = a;
     }
 }
@@ -210,7 +207,7 @@ __device__ __forceinline__ float warp_coef(const float* __restrict__ T, bool sep
 // inside the run is stored, a block shared with other runs is added
 // atomically (its slot was cleared by the run holding its first row).
 // smem: two ping-pong buffers in buf.
-__device__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int par) {
+__device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int par) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
     float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
@@ -258,7 +255,7 @@ __device__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int p
 // quadratic (20 values) and the block's frame (4 values).  Also clears the
 // next parity's moments of the blocks whose first row lies in this run
 // (levels >= 1).
-__device__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par) {
+__device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
     const float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
@@ -298,27 +295,61 @@ __device__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par
             dst[23] = g.w;
         }
     }
-    // levels 1..top: one warp per block, over all levels at once
+    // levels 1..top, all levels at once: separable blocks one thread each,
+    // coupled blocks (boundary edges inside) one warp each
     {
         int total = 0;
         for (int l = 1; l <= top; ++l) total += ((hi - 1) >> ml_shift(l)) - (lo >> ml_shift(l)) + 1;
-        for (int w = warp; w < total; w += nwarp) {
-            int l = 1, j = w;
-            while (true) {   // the level and block of work item w
+        auto item = [&](int w, int& l, int& j) {   // the level and block of work item w
+            l = 1;
+            j = w;
+            while (true) {
                 const int nbl = ((hi - 1) >> ml_shift(l)) - (lo >> ml_shift(l)) + 1;
                 if (j < nbl) break;
                 j -= nbl;
                 ++l;
             }
+        };
+        for (int w = threadIdx.x; w < total; w += blockDim.x) {
+            int l, j;
+            item(w, l, j);
             const int sh = ml_shift(l);
             const int blk = (lo >> sh) + j;
             const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            if (!a.sep[gb]) continue;
+            const float* src = Mp + gb * ML_NM;
+            const float* T = a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l);
+            float* dst = tab + (ml_capoff(l) + j) * 24;
+            float m[10], c[10];
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int f = 0; f < 10; ++f) m[f] = __ldcg(src + 10 * h + f);
+                tri_coef<10>(T, m, c);
+#pragma unroll
+                for (int f = 0; f < 10; ++f) dst[10 * h + f] = c[f];
+            }
+            if ((blk << sh) >= lo)   // first row here: clear the next parity
+#pragma unroll
+                for (int f = 0; f < ML_NM; ++f) Mn[gb * ML_NM + f] = 0.f;
+            const float4 g = a.geo[gb];
+            dst[20] = g.x;
+            dst[21] = g.y;
+            dst[22] = g.z;
+            dst[23] = g.w;
+        }
+        for (int w = warp; w < total; w += nwarp) {
+            int l, j;
+            item(w, l, j);
+            const int sh = ml_shift(l);
+            const int blk = (lo >> sh) + j;
+            const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            if (a.sep[gb]) continue;   // warp-uniform
             const float mL = lane < ML_NM ? __ldcg(Mp + gb * ML_NM + lane) : 0.f;
-            const float c = warp_coef(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l), a.sep[gb] != 0, mL);
+            const float c = warp_coef(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l), false, mL);
             float* dst = tab + (ml_capoff(l) + j) * 24;
             if (lane < ML_NM) {
                 dst[lane] = c;
-                if ((blk << sh) >= lo) Mn[gb * ML_NM + lane] = 0.f;   // first row here: clear the next parity
+                if ((blk << sh) >= lo) Mn[gb * ML_NM + lane] = 0.f;
             }
             if (lane == 0) {
                 const float4 g = a.geo[gb];
@@ -351,17 +382,20 @@ __device__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par
     }
 }
 
-// Level-0 moments of r for one 256-row pass (all lanes of the warp take part):
-// half-warp h holds one 16-row block; its lane 0 stores the 20 sums.
+// Level-0 moments of r for one 256-row pass (the warp's 32 rows are two
+// 16-row blocks): every row's 20 products go through shared memory (mbuf, 20
+// floats per thread), and lane l sums entry l % 20 of block l / 20 (then
+// l + 32) over the block's 16 rows and stores it.
 __device__ __forceinline__ void ml_moments0(const MlArgs& a, const DfRun& run, int base, int par, bool act, float d,
-                                            float rx, float ry, int row) {
+                                            float rx, float ry, int row, float* mbuf) {
+    const int lane = threadIdx.x & 31;
+    const int pv = a.pvoff[run.seg];
+    const int64_t g0 = a.lofs[0] + a.bofs[run.seg];
     float mom[ML_NM];
 #pragma unroll
     for (int f = 0; f < ML_NM; ++f) mom[f] = 0.f;
-    const int pv = a.pvoff[run.seg];
-    const int64_t g0 = a.lofs[0] + a.bofs[run.seg];
-    const int blk = (base + (int)(threadIdx.x & ~15u) - pv) >> 4;
     if (act && d != 0.f) {
+        const int blk = (row - pv) >> 4;
         const float4 g = a.geo[g0 + blk];
         const float sd = sqrtf(d);
         float mv[10];
@@ -374,20 +408,27 @@ __device__ __forceinline__ void ml_moments0(const MlArgs& a, const DfRun& run, i
             mom[10 + f] = mv[f] * uy;
         }
     }
+    float4* mine = reinterpret_cast<float4*>(mbuf + threadIdx.x * ML_NM);
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
+    for (int f = 0; f < ML_NM / 4; ++f) mine[f] = make_float4(mom[4 * f], mom[4 * f + 1], mom[4 * f + 2], mom[4 * f + 3]);
+    __syncwarp();
+    const int wbase = threadIdx.x & ~31u;   // this warp's first thread (and row offset in the pass)
 #pragma unroll
-        for (int f = 0; f < ML_NM; ++f) mom[f] += __shfl_xor_sync(0xffffffffu, mom[f], o);
-    if ((threadIdx.x & 15) == 0 && base + (int)(threadIdx.x & ~15u) < run.hi) {
-        float4* dst = reinterpret_cast<float4*>(a.M + ((int64_t)par * a.mstride + g0 + blk) * ML_NM);
+    for (int o = lane; o < 2 * ML_NM; o += 32) {
+        const int h = o / ML_NM, f = o - h * ML_NM;
+        const int r0 = base + wbase + 16 * h;   // first row of the block
+        if (r0 < run.hi) {
+            float v = 0.f;
 #pragma unroll
-        for (int f = 0; f < ML_NM / 4; ++f)
-            dst[f] = make_float4(mom[4 * f], mom[4 * f + 1], mom[4 * f + 2], mom[4 * f + 3]);
+            for (int r = 0; r < 16; ++r) v += mbuf[(wbase + 16 * h + r) * ML_NM + f];
+            a.M[((int64_t)par * a.mstride + g0 + ((r0 - pv) >> 4)) * ML_NM + f] = v;
+        }
     }
+    __syncwarp();
 }
 
 template <int MINB>
-__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(MlArgs a) {
+__global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_constant__ MlArgs a) {
     using A = ArithDF;
     using S = A::S;
     using V = A::V;
@@ -396,6 +437,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(MlArgs a) {
     __shared__ double sc[2][2];
     __shared__ int sflag[2][2];
     __shared__ __align__(16) float tab[ML_CAPTOT * 24];
+    __shared__ __align__(16) float mbuf[RUN_THREADS * ML_NM];
     const int nseg = a.nseg;
     const int rb = a.run_off[blockIdx.x], re = a.run_off[blockIdx.x + 1];
     const int32_t* __restrict__ rp = a.rp;
@@ -470,7 +512,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(MlArgs a) {
                 const bool act = row < run.hi;
                 const float d = act ? __ldg(dgp + row) : 0.f;
                 const V rv = act ? a.r[row] : A::vzero();
-                ml_moments0(a, run, base, 0, act, d, rv.x, rv.z, row);
+                ml_moments0(a, run, base, 0, act, d, rv.x, rv.z, row, mbuf);
             }
             __syncthreads();
             ml_restrict(a, run, tab, 0);
@@ -644,7 +686,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(MlArgs a) {
                         rd1 = fmaf(d * l1, l1, rd1);
                     }
                 }
-                ml_moments0(a, run, base, par, act, d, l0, l1, row);
+                ml_moments0(a, run, base, par, act, d, l0, l1, row, mbuf);
             }
             float2 pv[2] = {make_float2(rd0, 0.f), make_float2(rd1, 0.f)};
             double v[2];
