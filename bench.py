@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cold", action="store_true", help="skip the cold-start comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-mesh uneven batch (one GPU only)")
     ap.add_argument("--batch-meshes", type=int, default=256)
+    ap.add_argument("--no-sphere", action="store_true", help="skip the 655k-vertex sphere (one GPU only)")
     ap.add_argument("--local-precision", type=int, default=2,
                     help="DNCP solve: 0 FP64 PCG, 2 double-float PCG in FP64 refinement")
     return ap.parse_args()
@@ -172,6 +173,50 @@ def run_batch(api, torch, ms, steps: int, warmup: int) -> dict:
             "residual": {"dncp": st["dncp_relres"], "final": st["final_relres"]},
             "dncp_pcg": {"achieved_gbs": gbs, "launches": st_local["pcg_launches"]},
             "final_pcg": {"achieved_gbs": fb / (fms / 1000.0) / 1e9 if fms > 0 else None}}
+
+
+# ---------------------------------------------------------------- sphere
+
+SPHERE_WORKLOAD = ("genus-0 closed surface: icosahedron subdivided 8 times (655,362 vertices), radius 1 + 0.2 x real "
+                   "spherical harmonics to degree 6 (coefficients N(0,1)/(l+1)^2, seed 0), cut into 8 octants; "
+                   "spherical map (last weld closed), one batched launch per solve stage")
+
+
+def run_sphere(api, torch, steps: int, warmup: int, peak: float) -> dict:
+    """Throughput of the spherical variant (inputs resident in device memory)."""
+    from paper_1903_12359_gb300 import meshgen
+    m = meshgen.icosphere_sh_mesh(subdiv=8, seed=0)
+    Vd = torch.as_tensor(m.V, device="cuda")
+    Fd = torch.as_tensor(m.F, device="cuda", dtype=torch.int32)
+    Ld = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
+    out = torch.empty((m.nv, 3), dtype=torch.float64, device="cuda")
+    ctx = api.Context(variant=api.SPHERE, precision=api.FP32_REFINED, tol=TOL, local_precision=api.DF64_REFINED)
+    rows = []
+    for i in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        part = ctx.partition(Vd, Fd, face_labels=Ld, closed=True)
+        part.local_param()
+        st_local = part.get_stats()
+        part.weld()
+        part.global_solve(out)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        st = dict(part.stats)
+        part.free()
+        if i >= warmup:
+            rows.append((e0.elapsed_time(e1), st, st_local))
+    ms_step = sum(r[0] for r in rows) / len(rows)
+    st, st_local = rows[-1][1], rows[-1][2]
+    gbs = sum(r[2]["pcg_bytes"] for r in rows) / (sum(r[2]["pcg_ms"] for r in rows) / 1000.0) / 1e9
+    return {"workload": SPHERE_WORKLOAD, "nv": m.nv, "nf": m.nf, "pieces": st["K"], "value": m.nv / (ms_step / 1000.0),
+            "unit": "vertices/s", "ms_per_step": ms_step, "steps": len(rows), "tol": TOL,
+            "stages_ms": {k: st[k] for k in ("ms_partition", "ms_assembly", "ms_local", "ms_weld", "ms_final")},
+            "iterations": {"dncp": st["dncp_iters"], "final": st["final_iters"]},
+            "residual": {"dncp": st["dncp_relres"], "final": st["final_relres"]},
+            "dncp_pcg": {"achieved_gbs": gbs, "frac": gbs / peak, "launches": st_local["pcg_launches"]}}
 
 
 # ---------------------------------------------------------------- clocks
@@ -416,6 +461,9 @@ def main():
     batched = None
     if batch_meshes is not None:
         batched = run_batch(api, torch, batch_meshes, steps=2, warmup=1)
+    sphere = None
+    if ws == 1 and not args.no_sphere:
+        sphere = run_sphere(api, torch, steps=2, warmup=1, peak=measured_peaks().get("hbm_gbs") or 6800.0)
     if rank != 0:
         return 0
     peaks = measured_peaks()
@@ -477,6 +525,8 @@ def main():
         if batched["final_pcg"]["achieved_gbs"] is not None:
             batched["final_pcg"]["frac"] = batched["final_pcg"]["achieved_gbs"] / peak
         line["batched"] = batched
+    if sphere is not None:
+        line["sphere"] = sphere
     if cpu:
         line["cpu_baseline"] = {"value": cpu["nv"] / cpu["seconds"], "unit": "vertices/s", "cores": cpu["workers"],
                                 "kind": "oracle",

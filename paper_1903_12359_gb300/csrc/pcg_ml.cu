@@ -180,24 +180,26 @@ __device__ __forceinline__ void tri_coef(const float* __restrict__ T, const floa
 }
 
 // The same for one coarse block by a warp (N = 10 separable, applied to x and
-// y, or N = 20): lane L holds m_L on entry and c_L on return (L < 20).
+// y, or N = 20): lane L holds m_L on entry and c_L on return (L < 20).  Each
+// lane loads its column and row of T first, so the loads overlap.
 __device__ __forceinline__ float warp_coef(const float* __restrict__ T, bool sep, float mL) {
     const int lane = threadIdx.x & 31;
     const int n = sep ? 10 : 20;
     const int h = sep ? (lane >= 10 ? 10 : 0) : 0;   // first lane of this lane's system
     const int i = lane - h;                          // output index in the system
+    const bool on = lane < 20;
+    float colT[20], rowT[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) {
+        colT[k] = (on && k <= i && k < n) ? __ldg(T + ut(k, i, n)) : 0.f;
+        rowT[k] = (on && k >= i && k < n) ? __ldg(T + ut(i, k, n)) : 0.f;
+    }
     float u = 0.f;
 #pragma unroll
-    for (int k = 0; k < 20; ++k) {   // u_i = sum_{k <= i} T_ki m_k
-        const float mk = __shfl_sync(0xffffffffu, mL, (h + k) & 31);
-        if (k <= i && k < n && lane < 20) u = fmaf(__ldg(T + ut(k, i, n)), mk, u);
-    }
+    for (int k = 0; k < 20; ++k) u = fmaf(colT[k], __shfl_sync(0xffffffffu, mL, (h + k) & 31), u);   // sum_{k<=i} T_ki m_k
     float c = 0.f;
 #pragma unroll
-    for (int k = 0; k < 20; ++k) {   // c_i = sum_{k >= i} T_ik u_k
-        const float uk = __shfl_sync(0xffffffffu, u, (h + k) & 31);
-        if (k >= i && k < n && lane < 20) c = fmaf(__ldg(T + ut(i, k, n)), uk, c);
-    }
+    for (int k = 0; k < 20; ++k) c = fmaf(rowT[k], __shfl_sync(0xffffffffu, u, (h + k) & 31), c);    // sum_{k>=i} T_ik u_k
     return c;
 }
 
@@ -221,25 +223,33 @@ __device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, floa
         const int c0 = lo >> shc, c1 = (hi - 1) >> shc;
         const int64_t gb0 = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s];
         const int64_t gc0 = a.lofs[l - 1] + a.bofs[(l - 1) * (a.nseg + 1) + s];
-        for (int task = threadIdx.x; task < (b1 - b0 + 1) * ML_NM; task += blockDim.x) {
-            const int j = task / ML_NM, k = task - j * ML_NM;
-            const int h = k >= 10 ? 10 : 0;
+        for (int task = threadIdx.x; task < (b1 - b0 + 1) * 2; task += blockDim.x) {
+            const int j = task >> 1, h = (task & 1) * 10;
             const int blk = b0 + j;
             const float4 gp = a.geo[gb0 + blk];
-            float acc = 0.f;
+            float acc[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) acc[k] = 0.f;
             const int cl = max(blk * 4, c0), ch = min(blk * 4 + 3, c1);
             for (int c = cl; c <= ch; ++c) {
                 const float4 gc = a.geo[gc0 + c];
                 const float sc = gp.w / gc.w;
                 const float t[3] = {(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w, (gc.z - gp.z) * gp.w};
                 const float* src = (l == 1 ? Mp + (gc0 + c) * ML_NM : prev + (c - c0) * ML_NM) + h;
-                acc += mom_out(k - h, src, sc, t);
+                float mc[10];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) mc[k] = src[k];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) acc[k] += mom_out(k, mc, sc, t);
             }
-            cur[j * ML_NM + k] = acc;
-            float* g = Mp + (gb0 + blk) * ML_NM + k;
+            float* g = Mp + (gb0 + blk) * ML_NM + h;
             const bool inside = (blk << sh) >= lo && min((blk + 1) << sh, nrow) <= hi;
-            if (inside) *g = acc;
-            else atomicAdd(g, acc);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                cur[j * ML_NM + h + k] = acc[k];
+                if (inside) g[k] = acc[k];
+                else atomicAdd(g + k, acc[k]);
+            }
         }
         __syncthreads();
         float* t = prev;
@@ -368,15 +378,18 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
         const int pb0 = lo >> ml_shift(l + 1);
         float* tl = tab + ml_capoff(l) * 24;
         const float* tp = tab + ml_capoff(l + 1) * 24;
-        for (int task = threadIdx.x; task < (b1 - b0 + 1) * ML_NM; task += blockDim.x) {
-            const int j = task / ML_NM, k = task - j * ML_NM;
-            const int h = k >= 10 ? 10 : 0;
+        for (int task = threadIdx.x; task < (b1 - b0 + 1) * 2; task += blockDim.x) {
+            const int j = task >> 1, h = (task & 1) * 10;
             const int blk = b0 + j;
             float* dst = tl + j * 24;
             const float* pc = tp + ((blk >> 2) - pb0) * 24;
             const float sc = pc[23] / dst[23];
             const float t[3] = {(dst[20] - pc[20]) * pc[23], (dst[21] - pc[21]) * pc[23], (dst[22] - pc[22]) * pc[23]};
-            dst[k] += coef_out(k - h, pc + h, sc, t);
+            float cp[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) cp[k] = pc[h + k];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) dst[h + k] += coef_out(k, cp, sc, t);
         }
         __syncthreads();
     }
