@@ -1555,6 +1555,58 @@ int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* 
     return total;
 }
 
+// Runs for the preconditioned kernel: when every active piece holds at least
+// one block's share of the rows, each piece gets a whole number of blocks
+// (its share of `grid`, largest remainders first) and its rows are split
+// evenly among them at multiples of `align`, in runs of at most maxlen rows,
+// so no block straddles two pieces.  Otherwise make_runs.
+int64_t make_runs_by_piece(const std::vector<int64_t>& voff, const std::vector<uint8_t>* active, int grid,
+                           std::vector<DfRun>& runs, std::vector<int32_t>& roff, int align, int maxlen) {
+    std::vector<int> segs;
+    int64_t total = 0, smallest = INT64_MAX;
+    for (int i = 0; i + 1 < (int)voff.size(); ++i)
+        if (!active || (*active)[i]) {
+            segs.push_back(i);
+            total += voff[i + 1] - voff[i];
+            smallest = std::min<int64_t>(smallest, voff[i + 1] - voff[i]);
+        }
+    if (segs.empty() || (int)segs.size() > grid || smallest * grid < total)
+        return make_runs(voff, active, grid, runs, roff, align, maxlen);
+    std::vector<int> quota(segs.size());
+    std::vector<std::pair<double, int>> rem;
+    int used = 0;
+    for (size_t c = 0; c < segs.size(); ++c) {
+        const double share = (double)(voff[segs[c] + 1] - voff[segs[c]]) * grid / (double)total;
+        quota[c] = std::max(1, (int)share);
+        used += quota[c];
+        rem.push_back({share - (double)(int)share, (int)c});
+    }
+    std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first != y.first ? x.first > y.first : x.second < y.second;
+    });
+    for (size_t t = 0; used < grid && t < rem.size(); ++t, ++used) ++quota[rem[t].second];
+    runs.clear();
+    roff.assign(grid + 1, 0);
+    int b = 0;
+    for (size_t c = 0; c < segs.size() && b < grid; ++c) {
+        const int seg = segs[c];
+        const int64_t len = voff[seg + 1] - voff[seg];
+        for (int q = 0; q < quota[c] && b < grid; ++q, ++b) {
+            roff[b] = (int32_t)runs.size();
+            int64_t lo = len * q / quota[c], hi = len * (q + 1) / quota[c];
+            if (q > 0) lo = lo / align * align;
+            if (q + 1 < quota[c]) hi = hi / align * align;
+            for (int64_t a = lo; a < hi;) {
+                const int64_t e = maxlen > 0 ? std::min<int64_t>(hi, a + maxlen) : hi;
+                runs.push_back(DfRun{seg, (int32_t)(voff[seg] + a), (int32_t)(voff[seg] + e), 0, 0, 0, 0, 0});
+                a = e;
+            }
+        }
+    }
+    for (; b <= grid; ++b) roff[b] = (int32_t)runs.size();
+    return total;
+}
+
 void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, DfSystem& D) {
     cudaStream_t s = ctx->stream;
     const int64_t n = P.Nc;
@@ -1598,7 +1650,8 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     D.grid = grid;
     std::vector<DfRun> runs;
     std::vector<int32_t> roff;
-    D.covered = D.ml ? make_runs(P.voff, nullptr, grid, runs, roff, 16, ML_SEG) : make_runs(P.voff, nullptr, grid, runs, roff);
+    D.covered = D.ml ? make_runs_by_piece(P.voff, nullptr, grid, runs, roff, 16, ML_SEG)
+                     : make_runs(P.voff, nullptr, grid, runs, roff);
     D.nruns = (int32_t)runs.size();
     if (D.sched == 4)
         for (int b = 0; b < grid; ++b)
@@ -1692,7 +1745,7 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     auto set_runs = [&](const std::vector<uint8_t>* active) {
         std::vector<DfRun> runs;
         std::vector<int32_t> roff;
-        D.covered = D.ml ? make_runs(P.voff, active, D.grid, runs, roff, 16, ML_SEG)
+        D.covered = D.ml ? make_runs_by_piece(P.voff, active, D.grid, runs, roff, 16, ML_SEG)
                          : make_runs(P.voff, active, D.grid, runs, roff);
         if ((int64_t)runs.size() > D.runs_cap) fail(PGCP_E_CUDA, "rebuilt PCG runs exceed their buffer");
         D.nruns = (int32_t)runs.size();

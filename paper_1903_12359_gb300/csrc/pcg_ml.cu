@@ -208,8 +208,9 @@ __device__ __forceinline__ float warp_coef(const float* __restrict__ T, bool sep
 // from this run's rows, one (block, moment) per thread, summed into M: a block
 // inside the run is stored, a block shared with other runs is added
 // atomically (its slot was cleared by the run holding its first row).
-// smem: two ping-pong buffers in buf.
-__device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int par) {
+// smem: two ping-pong buffers in buf; the block frames come from tab when
+// it still holds this run's tables (else from global memory).
+__device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, float* buf, int par, const float* tab) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
     float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
@@ -226,13 +227,14 @@ __device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, floa
         for (int task = threadIdx.x; task < (b1 - b0 + 1) * 2; task += blockDim.x) {
             const int j = task >> 1, h = (task & 1) * 10;
             const int blk = b0 + j;
-            const float4 gp = a.geo[gb0 + blk];
+            const float4 gp = tab ? *reinterpret_cast<const float4*>(tab + (ml_capoff(l) + j) * 24 + 20) : a.geo[gb0 + blk];
             float acc[10];
 #pragma unroll
             for (int k = 0; k < 10; ++k) acc[k] = 0.f;
             const int cl = max(blk * 4, c0), ch = min(blk * 4 + 3, c1);
             for (int c = cl; c <= ch; ++c) {
-                const float4 gc = a.geo[gc0 + c];
+                const float4 gc = tab ? *reinterpret_cast<const float4*>(tab + (ml_capoff(l - 1) + c - c0) * 24 + 20)
+                                      : a.geo[gc0 + c];
                 const float sc = gp.w / gc.w;
                 const float t[3] = {(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w, (gc.z - gp.z) * gp.w};
                 const float* src = (l == 1 ? Mp + (gc0 + c) * ML_NM : prev + (c - c0) * ML_NM) + h;
@@ -400,7 +402,7 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
 // floats per thread), and lane l sums entry l % 20 of block l / 20 (then
 // l + 32) over the block's 16 rows and stores it.
 __device__ __forceinline__ void ml_moments0(const MlArgs& a, const DfRun& run, int base, int par, bool act, float d,
-                                            float rx, float ry, int row, float* mbuf) {
+                                            float rx, float ry, int row, float* mbuf, const float* tab) {
     const int lane = threadIdx.x & 31;
     const int pv = a.pvoff[run.seg];
     const int64_t g0 = a.lofs[0] + a.bofs[run.seg];
@@ -409,7 +411,8 @@ __device__ __forceinline__ void ml_moments0(const MlArgs& a, const DfRun& run, i
     for (int f = 0; f < ML_NM; ++f) mom[f] = 0.f;
     if (act && d != 0.f) {
         const int blk = (row - pv) >> 4;
-        const float4 g = a.geo[g0 + blk];
+        const float4 g = tab ? *reinterpret_cast<const float4*>(tab + (blk - ((run.lo - pv) >> 4)) * 24 + 20)
+                             : a.geo[g0 + blk];
         const float sd = sqrtf(d);
         float mv[10];
         mono10<float>((a.xr[3 * row] - g.x) * g.w, (a.xr[3 * row + 1] - g.y) * g.w, (a.xr[3 * row + 2] - g.z) * g.w,
@@ -451,6 +454,9 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
     __shared__ int sflag[2][2];
     __shared__ __align__(16) float tab[ML_CAPTOT * 24];
     __shared__ __align__(16) float mbuf[RUN_THREADS * ML_NM];
+    __shared__ int tab_run;   // the run whose tables tab holds (-1: none)
+    if (threadIdx.x == 0) tab_run = -1;
+    __syncthreads();
     const int nseg = a.nseg;
     const int rb = a.run_off[blockIdx.x], re = a.run_off[blockIdx.x + 1];
     const int32_t* __restrict__ rp = a.rp;
@@ -474,6 +480,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
             __syncthreads();
             if (skip) continue;
             ml_tables(a, run, tab, par);
+            if (threadIdx.x == 0) tab_run = ri;
             const int pv = a.pvoff[s];
             const int c0 = (run.lo - pv) >> 4;
             S rz0 = A::zero(), rz1 = A::zero();
@@ -525,10 +532,10 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                 const bool act = row < run.hi;
                 const float d = act ? __ldg(dgp + row) : 0.f;
                 const V rv = act ? a.r[row] : A::vzero();
-                ml_moments0(a, run, base, 0, act, d, rv.x, rv.z, row, mbuf);
+                ml_moments0(a, run, base, 0, act, d, rv.x, rv.z, row, mbuf, nullptr);
             }
             __syncthreads();
-            ml_restrict(a, run, tab, 0);
+            ml_restrict(a, run, mbuf, 0, nullptr);
         }
         grid.sync();
         phase_c(0, 0);
@@ -671,6 +678,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
             if (sflag[slot][0]) continue;
             const S al0 = A::from_d(sc[slot][0]), al1 = A::from_d(sc[slot][1]);
             const S nal0 = A::neg(al0), nal1 = A::neg(al1);
+            const float* tab_here = tab_run == ri ? tab : nullptr;   // this run's frames, from the last phase C
             float rd0 = 0.f, rd1 = 0.f;
             for (int base = run.lo; base < run.hi; base += blockDim.x) {
                 if (base + (int)(threadIdx.x & ~31u) >= run.hi) continue;   // warp beyond the run
@@ -699,7 +707,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                         rd1 = fmaf(d * l1, l1, rd1);
                     }
                 }
-                ml_moments0(a, run, base, par, act, d, l0, l1, row, mbuf);
+                ml_moments0(a, run, base, par, act, d, l0, l1, row, mbuf, tab_here);
             }
             float2 pv[2] = {make_float2(rd0, 0.f), make_float2(rd1, 0.f)};
             double v[2];
@@ -709,7 +717,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                 atomicAdd(&RDn[2 * s + 1], v[1]);
             }
             __syncthreads();
-            ml_restrict(a, run, tab, par);
+            ml_restrict(a, run, mbuf, par, tab_here);
         }
         grid.sync();
         // ---------------- phase C: z = M r, <r, z>
