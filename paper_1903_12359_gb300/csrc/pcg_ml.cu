@@ -65,7 +65,6 @@ __host__ __device__ constexpr int ml_capoff(int l) {
     return o;
 }
 constexpr int ML_CAPTOT = ml_capoff(ML_MAXL);
-constexpr int ML_STAGE = RUN_THREADS * ML_NM;   // floats of the per-pass transpose buffer, reused as staging
 
 // packed upper-triangular index (row-major upper triangle of an n x n matrix)
 __host__ __device__ __forceinline__ int ut(int i, int j, int n) { return i * n - i * (i - 1) / 2 + (j - i); }
@@ -180,26 +179,6 @@ __device__ __forceinline__ void tri_coef(const float* __restrict__ T, const floa
     }
 }
 
-// The same with T in shared memory.
-template <int N>
-__device__ __forceinline__ void tri_coef_s(const float* T, const float* m, float* c) {
-    float u[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        float a = 0.f;
-#pragma unroll
-        for (int i = 0; i <= j; ++i) a = fmaf(T[ut(i, j, N)], m[i], a);
-        u[j] = a;
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        float a = 0.f;
-#pragma unroll
-        for (int j = i; j < N; ++j) a = fmaf(T[ut(i, j, N)], u[j], a);
-        c[i] = a;
-    }
-}
-
 // The same for one coarse block by a warp (N = 10 separable, applied to x and
 // y, or N = 20): lane L holds m_L on entry and c_L on return (L < 20).  Each
 // lane loads its column and row of T first, so the loads overlap.
@@ -253,25 +232,17 @@ __device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, floa
 #pragma unroll
             for (int k = 0; k < 10; ++k) acc[k] = 0.f;
             const int cl = max(blk * 4, c0), ch = min(blk * 4 + 3, c1);
-            float mc[4][10];
-            float4 gc[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {   // the (up to four) children's moments and frames, loaded together
-                const int c = blk * 4 + q;
-                const bool ok = c >= cl && c <= ch;
+            for (int c = cl; c <= ch; ++c) {
+                const float4 gc = tab ? *reinterpret_cast<const float4*>(tab + (ml_capoff(l - 1) + c - c0) * 24 + 20)
+                                      : a.geo[gc0 + c];
+                const float sc = gp.w / gc.w;
+                const float t[3] = {(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w, (gc.z - gp.z) * gp.w};
                 const float* src = (l == 1 ? Mp + (gc0 + c) * ML_NM : prev + (c - c0) * ML_NM) + h;
-                gc[q] = ok ? (tab ? *reinterpret_cast<const float4*>(tab + (ml_capoff(l - 1) + c - c0) * 24 + 20)
-                                  : a.geo[gc0 + c])
-                           : make_float4(0.f, 0.f, 0.f, 1.f);
+                float mc[10];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) mc[q][k] = ok ? src[k] : 0.f;
-            }
+                for (int k = 0; k < 10; ++k) mc[k] = src[k];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float sc = gp.w / gc[q].w;
-                const float t[3] = {(gc[q].x - gp.x) * gp.w, (gc[q].y - gp.y) * gp.w, (gc[q].z - gp.z) * gp.w};
-#pragma unroll
-                for (int k = 0; k < 10; ++k) acc[k] += mom_out(k, mc[q], sc, t);
+                for (int k = 0; k < 10; ++k) acc[k] += mom_out(k, mc, sc, t);
             }
             float* g = Mp + (gb0 + blk) * ML_NM + h;
             const bool inside = (blk << sh) >= lo && min((blk + 1) << sh, nrow) <= hi;
@@ -296,7 +267,7 @@ __device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, floa
 // quadratic (20 values) and the block's frame (4 values).  Also clears the
 // next parity's moments of the blocks whose first row lies in this run
 // (levels >= 1).
-__device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par, float* stage) {
+__device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float* tab, int par) {
     const int s = run.seg, pv = a.pvoff[s];
     const int top = min(a.ltop[s], a.nl - 1);
     const float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
@@ -351,50 +322,32 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
                 ++l;
             }
         };
-        // separable blocks: factors (55) and moments (20) staged in `stage`, in
-        // chunks, with coalesced loads, then one thread per block
-        constexpr int SPAN = 55 + ML_NM;
-        const int chunk = ML_STAGE / SPAN;
-        for (int w0 = 0; w0 < total; w0 += chunk) {
-            const int nw = min(chunk, total - w0);
-            for (int e = threadIdx.x; e < nw * SPAN; e += blockDim.x) {
-                const int wl = e / SPAN, f = e - wl * SPAN;
-                int l, j;
-                item(w0 + wl, l, j);
-                const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + (lo >> ml_shift(l)) + j;
-                if (!a.sep[gb]) continue;
-                stage[e] = f < 55 ? __ldg(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l) + f)
-                                  : __ldcg(Mp + gb * ML_NM + (f - 55));
+        for (int w = threadIdx.x; w < total; w += blockDim.x) {
+            int l, j;
+            item(w, l, j);
+            const int sh = ml_shift(l);
+            const int blk = (lo >> sh) + j;
+            const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            if (!a.sep[gb]) continue;
+            const float* src = Mp + gb * ML_NM;
+            const float* T = a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l);
+            float* dst = tab + (ml_capoff(l) + j) * 24;
+            float m[10], c[10];
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int f = 0; f < 10; ++f) m[f] = __ldcg(src + 10 * h + f);
+                tri_coef<10>(T, m, c);
+#pragma unroll
+                for (int f = 0; f < 10; ++f) dst[10 * h + f] = c[f];
             }
-            __syncthreads();
-            for (int wl = threadIdx.x; wl < nw; wl += blockDim.x) {
-                int l, j;
-                item(w0 + wl, l, j);
-                const int sh = ml_shift(l);
-                const int blk = (lo >> sh) + j;
-                const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
-                if (!a.sep[gb]) continue;
-                const float* T = stage + wl * SPAN;
-                const float* mm = T + 55;
-                float* dst = tab + (ml_capoff(l) + j) * 24;
-                float m[10], c[10];
-                for (int h = 0; h < 2; ++h) {
+            if ((blk << sh) >= lo)   // first row here: clear the next parity
 #pragma unroll
-                    for (int f = 0; f < 10; ++f) m[f] = mm[10 * h + f];
-                    tri_coef_s<10>(T, m, c);
-#pragma unroll
-                    for (int f = 0; f < 10; ++f) dst[10 * h + f] = c[f];
-                }
-                if ((blk << sh) >= lo)   // first row here: clear the next parity
-#pragma unroll
-                    for (int f = 0; f < ML_NM; ++f) Mn[gb * ML_NM + f] = 0.f;
-                const float4 g = a.geo[gb];
-                dst[20] = g.x;
-                dst[21] = g.y;
-                dst[22] = g.z;
-                dst[23] = g.w;
-            }
-            __syncthreads();
+                for (int f = 0; f < ML_NM; ++f) Mn[gb * ML_NM + f] = 0.f;
+            const float4 g = a.geo[gb];
+            dst[20] = g.x;
+            dst[21] = g.y;
+            dst[22] = g.z;
+            dst[23] = g.w;
         }
         for (int w = warp; w < total; w += nwarp) {
             int l, j;
@@ -526,7 +479,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
             const bool skip = sflag[0][0];
             __syncthreads();
             if (skip) continue;
-            ml_tables(a, run, tab, par, mbuf);
+            ml_tables(a, run, tab, par);
             if (threadIdx.x == 0) tab_run = ri;
             const int pv = a.pvoff[s];
             const int c0 = (run.lo - pv) >> 4;
