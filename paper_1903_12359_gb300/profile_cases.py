@@ -12,6 +12,7 @@
         timed ones (CUDA events); checked against FP32 torch.
 
 Usage: python -m paper_1903_12359_gb300.profile_cases dncp --n 1000000 --max-iters 300 [--local-precision 0|2]
+       [--precond 0|1]  (0: multilevel preconditioner, 1: Jacobi)
        python -m paper_1903_12359_gb300.profile_cases gemm --rows 1048576 --reps 20
 """
 import argparse
@@ -30,6 +31,7 @@ def main(argv=None):
     ap.add_argument("--local-precision", type=int, default=2, help="0 FP64 PCG, 2 double-float PCG")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="mixed-precision PCG kernel variant: 3 or 4")
     ap.add_argument("--schedule", type=int, default=0, help="mixed-precision PCG schedule: 1 static, 2 dynamic")
+    ap.add_argument("--precond", type=int, default=0, help="double-float DNCP preconditioner: 0 multilevel, 1 Jacobi")
     a = ap.parse_args(argv)
     import torch
     from paper_1903_12359_gb300 import api, build, meshgen
@@ -63,7 +65,7 @@ def main(argv=None):
     if a.case == "dncp":
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10, max_iters=a.max_iters,
                           max_refine=1, local_precision=a.local_precision,
-                          pcg_blocks_per_sm=a.blocks_per_sm, pcg_schedule=a.schedule)
+                          pcg_blocks_per_sm=a.blocks_per_sm, pcg_schedule=a.schedule, local_precond=a.precond)
         part = ctx.partition(V, F, face_labels=L)
         try:
             part.local_param()
@@ -80,7 +82,7 @@ def main(argv=None):
     else:
         ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=1e-10,
                           local_precision=a.local_precision, pcg_blocks_per_sm=a.blocks_per_sm,
-                          pcg_schedule=a.schedule)
+                          pcg_schedule=a.schedule, local_precond=a.precond)
         part = ctx.partition(V, F, face_labels=L)
         part.local_param()
         part.weld()
