@@ -477,11 +477,11 @@ def main():
     dncp_iters = sum(s["dncp_iters"] for s in stats)
     achieved = pcg_bytes / (pcg_ms / 1000.0) / 1e9 if pcg_ms > 0 else 0.0
     df = args.local_precision == 2
-    kname = "k_pcg_run<ArithDF>" if df else "k_pcg<double,1>"
-    tr = ncu_traffic(kname, os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg_df.cu" if df else "pcg.cu"))
+    kname = "k_pcg_ml" if df else "k_pcg<double,1>"
+    tr = ncu_traffic(kname, os.path.join(ROOT, "paper_1903_12359_gb300", "csrc", "pcg_ml.cu" if df else "pcg.cu"))
     peak = hbm if hbm else 6800.0
-    kdesc = ("k_pcg_run<ArithDF> (persistent batched double-float PCG in FP64 refinement, local DNCP solves)" if df
-             else "k_pcg<double,1> (persistent batched FP64 PCG, local DNCP solves)")
+    kdesc = ("k_pcg_ml (persistent batched double-float PCG with the multilevel preconditioner, in FP64 refinement; "
+             "local DNCP solves)" if df else "k_pcg<double,1> (persistent batched FP64 PCG, local DNCP solves)")
     roofline = {"kernel": kdesc, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured (burst copy)" if hbm else "fallback",
@@ -489,8 +489,10 @@ def main():
                 "traffic_note": (tr.get("note") if tr else "no ncu capture of the current kernel source"),
                 "algorithmic_bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
                 "touched_bytes_per_launch": pcg_touched / max(pcg_launches, 1),
-                "bytes_note": "achieved counts the algorithmic bytes of a 2-RHS PCG iteration (240 B per "
-                              "double-float row at 7 entries, 136 B FP32); touched = what the kernel "
+                "bytes_note": "achieved counts the algorithmic bytes of a 2-RHS PCG iteration: 240 B per "
+                              "double-float row at 7 entries (Jacobi), plus z written and read, the vertex "
+                              "position and the preconditioner's block tables (about 300 B) with the "
+                              "multilevel preconditioner; 136 B per FP32 row; touched = what the kernel "
                               "schedule streams",
                 "avg_launch_ms": pcg_ms / max(pcg_launches, 1), "launches": pcg_launches,
                 "share_of_step": (pcg_ms / ms) if ms > 0 else None,
