@@ -203,6 +203,18 @@ __device__ __forceinline__ float warp_coef(const float* __restrict__ T, bool sep
     return c;
 }
 
+// First global block of each level of piece s (lofs + bofs), loaded once per
+// call into shared memory by threads 0 .. ML_MAXL-1; out also gets the
+// level's first packed-factor entry.  Ends with a barrier.
+__device__ __forceinline__ void ml_bases(const MlArgs& a, int s, int64_t* gb, int64_t* tf) {
+    if (threadIdx.x < ML_MAXL) {
+        const int l = threadIdx.x;
+        gb[l] = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s];
+        tf[l] = a.tofs[l] - a.lofs[l] * (int64_t)ml_ts(l);   // T of global block g: T + tf[l] + g * ts(l)
+    }
+    __syncthreads();
+}
+
 // Restriction for one run: after the level-0 moments of the run's rows are
 // stored (one half-warp per 16-row block), the coarser levels' partial moments
 // from this run's rows, one (block, moment) per thread, summed into M: a block
@@ -216,14 +228,16 @@ __device__ __noinline__ void ml_restrict(const MlArgs& a, const DfRun& run, floa
     float* Mp = a.M + (int64_t)par * a.mstride * ML_NM;
     const int lo = run.lo - pv, hi = run.hi - pv;
     const int nrow = a.pvoff[s + 1] - pv;
+    __shared__ int64_t s_gb[ML_MAXL], s_tf[ML_MAXL];
+    ml_bases(a, s, s_gb, s_tf);
     float* prev = buf;
     float* cur = buf + ml_cap(1) * ML_NM;
     for (int l = 1; l <= top; ++l) {
         const int sh = ml_shift(l), shc = ml_shift(l - 1);
         const int b0 = lo >> sh, b1 = (hi - 1) >> sh;
         const int c0 = lo >> shc, c1 = (hi - 1) >> shc;
-        const int64_t gb0 = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s];
-        const int64_t gc0 = a.lofs[l - 1] + a.bofs[(l - 1) * (a.nseg + 1) + s];
+        const int64_t gb0 = s_gb[l];
+        const int64_t gc0 = s_gb[l - 1];
         for (int task = threadIdx.x; task < (b1 - b0 + 1) * 2; task += blockDim.x) {
             const int j = task >> 1, h = (task & 1) * 10;
             const int blk = b0 + j;
@@ -274,10 +288,12 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
     float* Mn = a.M + (int64_t)(par ^ 1) * a.mstride * ML_NM;
     const int lo = run.lo - pv, hi = run.hi - pv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    __shared__ int64_t s_gb[ML_MAXL], s_tf[ML_MAXL];
+    ml_bases(a, s, s_gb, s_tf);
     // level 0: one thread per block
     {
         const int b0 = lo >> 4, b1 = (hi - 1) >> 4;
-        const int64_t gb0 = a.lofs[0] + a.bofs[s];
+        const int64_t gb0 = s_gb[0];
         for (int j = threadIdx.x; j <= b1 - b0; j += blockDim.x) {
             const int64_t gb = gb0 + b0 + j;
             const float* src = Mp + gb * ML_NM;
@@ -287,7 +303,7 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
                 m[f] = __ldcg(src + f);
                 m[4 + f] = __ldcg(src + 10 + f);
             }
-            const float* T = a.T + a.tofs[0] + (gb - a.lofs[0]) * ml_ts(0);
+            const float* T = a.T + s_tf[0] + gb * ml_ts(0);
             if (a.sep[gb]) {
                 tri_coef<4>(T, m, c);
                 tri_coef<4>(T, m + 4, c + 4);
@@ -327,10 +343,10 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
             item(w, l, j);
             const int sh = ml_shift(l);
             const int blk = (lo >> sh) + j;
-            const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            const int64_t gb = s_gb[l] + blk;
             if (!a.sep[gb]) continue;
             const float* src = Mp + gb * ML_NM;
-            const float* T = a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l);
+            const float* T = a.T + s_tf[l] + gb * ml_ts(l);
             float* dst = tab + (ml_capoff(l) + j) * 24;
             float m[10], c[10];
             for (int h = 0; h < 2; ++h) {
@@ -354,10 +370,10 @@ __device__ __noinline__ void ml_tables(const MlArgs& a, const DfRun& run, float*
             item(w, l, j);
             const int sh = ml_shift(l);
             const int blk = (lo >> sh) + j;
-            const int64_t gb = a.lofs[l] + a.bofs[l * (a.nseg + 1) + s] + blk;
+            const int64_t gb = s_gb[l] + blk;
             if (a.sep[gb]) continue;   // warp-uniform
             const float mL = lane < ML_NM ? __ldcg(Mp + gb * ML_NM + lane) : 0.f;
-            const float c = warp_coef(a.T + a.tofs[l] + (gb - a.lofs[l]) * ml_ts(l), false, mL);
+            const float c = warp_coef(a.T + s_tf[l] + gb * ml_ts(l), false, mL);
             float* dst = tab + (ml_capoff(l) + j) * 24;
             if (lane < ML_NM) {
                 dst[lane] = c;
