@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(128) k_ml_gram(int l, int nb, int nseg, const 
                 for (int q = 0; q < NF1; ++q) acc[p * NF1 + q] += mi[p] * v[q];
         }
     }
-    // block reduction: warps by shuffles, then across the 4 warps
+    // block reduction: warps by shuffles, then across the block's warps (1 to 4)
     __shared__ double sh[4][NO];
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
@@ -941,8 +941,12 @@ __global__ void __launch_bounds__(128) k_ml_gram(int l, int nb, int nseg, const 
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][i] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < NO; i += blockDim.x)
-        out[(int64_t)b * NO + i] = sh[0][i] + sh[1][i] + sh[2][i] + sh[3][i];
+    const int nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < NO; i += blockDim.x) {
+        double v = sh[0][i];
+        for (int w = 1; w < nw; ++w) v += sh[w][i];
+        out[(int64_t)b * NO + i] = v;
+    }
 }
 
 // Upper-triangular R (n x n, row-major full storage) with C ~ R^T R, dropping
@@ -1072,11 +1076,13 @@ void gram_level(cudaStream_t s, int l, int nb, int K, const DfSystem& D, const P
     GL.alloc((size_t)nb * NS, s);
     GK.alloc((size_t)nb * NF1 * NF1, s);
     const int32_t* bofs_l = D.ml_bofs.p + l * (K + 1);
-    { k_ml_gram<NF1, 0><<<nb, 128, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
+    // threads per block sized to the block's rows (16 * 4^l): 32 up to 64 rows, 64 for 256, else 128
+    const int nthr = l <= 1 ? 32 : (l == 2 ? 64 : 128);
+    { k_ml_gram<NF1, 0><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
                                             P.val64.p, P.diag64.p, fixed, P.nb.p, Cs.p); ::pgcp::note_launch(); }
-    { k_ml_gram<NF1, 1><<<nb, 128, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
+    { k_ml_gram<NF1, 1><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
                                             P.val64.p, P.diag64.p, fixed, P.nb.p, GL.p); ::pgcp::note_launch(); }
-    { k_ml_gram<NF1, 2><<<nb, 128, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
+    { k_ml_gram<NF1, 2><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
                                             P.val64.p, P.diag64.p, fixed, P.nb.p, GK.p); ::pgcp::note_launch(); }
     { k_ml_factor<NF1><<<nb, 32, 0, s>>>(nb, Cs.p, GL.p, GK.p, T, sep); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
