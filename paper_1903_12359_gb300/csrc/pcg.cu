@@ -621,6 +621,22 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         const double itol2 = o.inner_tol * o.inner_tol;
         DfSystem D;
         df_build(ctx, P, dncp, fixed, f32, D);
+        // Double-float on the static schedule: every refinement step reduces
+        // its own FP64 residual by DF_STEP and the next step continues the same
+        // CG with the residual replaced (df_solve).  The replacement must stay a
+        // small change of the recurrence residual for the search direction to
+        // remain usable, so a step stops long before the recurrence drifts away
+        // from the true residual (which happens near 2^-48 cond(A~)).
+        constexpr double DF_STEP = 1e-3;
+        const bool df_resume = !f32 && D.sched == 1 && !D.det;
+        // Safeguard: near the double-float floor a continued step can break
+        // down.  A step that leaves the worst FP64 residual above where it
+        // started is undone (x from before the step) and the next step
+        // restarts CG.
+        DBuf<double2> xsave;
+        if (df_resume) xsave.alloc(n, s);
+        double prev_worst = INFINITY;
+        bool restart = false;
         for (int outer = 0; outer < std::max(1, o.max_refine); ++outer) {
             RRo.zero();
             { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,
@@ -630,6 +646,18 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
             res.relres = relres_of(hRR, &ok);
             res.refine = outer;
             if (ok) return res;
+            if (df_resume && outer > 0 && res.relres > prev_worst) {
+                PGCP_CUDA(cudaMemcpyAsync(x, xsave.p, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+                RRo.zero();
+                { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p,
+                                                              dinv64.p, P.nb.p, dncp, x, 0, r64.p, RRo.p, nullptr,
+                                                              nullptr, tp); ::pgcp::note_launch(); }
+                fetch(RRo, hRR);
+                res.relres = relres_of(hRR, &ok);
+                restart = true;
+            }
+            if (df_resume) PGCP_CUDA(cudaMemcpyAsync(xsave.p, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+            prev_worst = res.relres;
             // thresholds on the inner residual: the final tolerance (double-float),
             // or a fixed reduction of this right-hand side (FP32); converged
             // pieces (coordinates) are frozen
@@ -639,11 +667,12 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
                     bool conv;
                     if (dncp) conv = hRR[2 * i] + hRR[2 * i + 1] <= tol2 * (hBB[2 * i] + hBB[2 * i + 1]);
                     else conv = hRR[j] <= tol2 * hBB[j];
-                    hTHR[j] = conv ? INFINITY
-                                   : (f32 ? std::max(itol2 * hRR[j], 0.25 * tol2 * hBB[j]) : 0.25 * tol2 * hBB[j]);
+                    const double step2 = f32 ? itol2 : (df_resume ? DF_STEP * DF_STEP : 0.0);
+                    hTHR[j] = conv ? INFINITY : std::max(step2 * hRR[j], 0.25 * tol2 * hBB[j]);
                 }
             }
-            res.iters += df_solve(ctx, P, D, r64.p, x, hTHR, o.max_iters);
+            res.iters += df_solve(ctx, P, D, r64.p, x, hTHR, o.max_iters, df_resume && outer > 0 && !restart);
+            restart = false;
         }
         RRo.zero();
         { k_residual<double, double2><<<nt, 256, 0, s>>>(d_tiles.p, P.row_ptr.p, P.col.p, P.val64.p, dinv64.p,

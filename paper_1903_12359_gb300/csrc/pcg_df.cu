@@ -102,6 +102,10 @@ struct RunArgs {
     // static schedule: first iteration of this launch (a solve may run as several
     // launches, the later ones over the rows of the unconverged pieces only)
     int32_t k0;
+    // k0 continues a solve whose residual was replaced: beta of iteration k0
+    // divides by RRP, each piece's <r, r> of its last active iteration
+    int32_t resume;
+    double* RRP;                        // [2 nseg]
     // deterministic mode (static schedule): every run stores its partial sums,
     // and a piece's total is summed over its runs in run order where needed
     int32_t det;
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
     int k = a.k0;
     for (; k < a.max_iters; ++k) {
         const double* RRk = a.RR + (k % 3) * 2 * nseg;
-        const double* RRm = a.RR + ((k + 2) % 3) * 2 * nseg;
+        const double* RRm = (a.resume && k == a.k0) ? a.RRP : a.RR + ((k + 2) % 3) * 2 * nseg;
         const double* RDk = a.RD + (k % 3) * 2 * nseg;
         double* PQk = a.PQ + (k % 2) * 2 * nseg;
         // ---------------- phase B: p = r + beta p, q = A~ r + beta q, <p, q>
@@ -374,6 +378,10 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
                 sc[slot][0] = al0;
                 sc[slot][1] = al1;
                 sflag[slot][0] = d0 && d1;
+                if (!(d0 && d1)) {   // the <r, r> this step used, kept for a resumed solve
+                    a.RRP[2 * s] = __ldcg(RRk + 2 * s);
+                    a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
+                }
             }
             __syncthreads();
             if (sflag[slot][0]) continue;
@@ -1325,7 +1333,7 @@ __global__ void k_run_prep(const DfRun* __restrict__ runs, const int32_t* __rest
                            const double2* __restrict__ r64, const double* __restrict__ sc, typename A::V* __restrict__ x,
                            typename A::V* __restrict__ r, typename A::V* __restrict__ p, typename A::V* __restrict__ q,
                            double* __restrict__ RR, double* __restrict__ RD, double* __restrict__ PRR0,
-                           double* __restrict__ PRD0) {
+                           double* __restrict__ PRD0, int keep_pq) {
     __shared__ double red[4 * (RUN_THREADS / 32)];
     for (int ri = run_off[blockIdx.x]; ri < run_off[blockIdx.x + 1]; ++ri) {
         const DfRun run = runs[ri];
@@ -1336,8 +1344,10 @@ __global__ void k_run_prep(const DfRun* __restrict__ runs, const int32_t* __rest
             const double a0 = si * ri64.x, a1 = si * ri64.y;
             const typename A::S f0 = A::from_d(a0), f1 = A::from_d(a1);
             x[i] = A::vzero();
-            p[i] = A::vzero();
-            q[i] = A::vzero();
+            if (!keep_pq) {
+                p[i] = A::vzero();
+                q[i] = A::vzero();
+            }
             r[i] = A::pack(f0, f1);
             if (si != 0.0) {
                 // the stored (rounded) values, so CG starts from what it iterates on
@@ -1423,17 +1433,21 @@ void build_typed(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, DfSyste
     D.q.alloc(n * vb, s);
 }
 
+// x~ = 0 and r~ = S r64; <r~, r~> and the unscaled sum of r64^2 go to slot
+// `slot` of RR and RD.  A resumed solve keeps p and q (residual replacement).
 template <typename A>
-void prep_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64) {
+void prep_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, int slot, bool resume) {
     cudaStream_t s = ctx->stream;
     using V = typename A::V;
     V* xv = reinterpret_cast<V*>(D.x.p);
     V* rv = reinterpret_cast<V*>(D.r.p);
     V* pv = reinterpret_cast<V*>(D.p.p);
     V* qv = reinterpret_cast<V*>(D.q.p);
-    { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, D.RR.p,
-                                                            D.RD.p, D.det ? D.PRR.p : nullptr,
-                                                            D.det ? D.PRD.p : nullptr); ::pgcp::note_launch(); }
+    double* RRs = D.RR.p + (int64_t)slot * 2 * P.K;
+    double* RDs = D.RD.p + (int64_t)slot * 2 * P.K;
+    { k_run_prep<A><<<(unsigned)D.grid, RUN_THREADS, 0, s>>>(D.runs.p, D.run_off.p, r64, D.sc.p, xv, rv, pv, qv, RRs,
+                                                            RDs, D.det ? D.PRR.p : nullptr,
+                                                            D.det ? D.PRD.p : nullptr, resume ? 1 : 0); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
     if (D.sched >= 2) {
         { k_dyn_init<<<(unsigned)std::max<int64_t>(1, ceil_div((int64_t)P.K, 256)), 256, 0, s>>>(
@@ -1448,7 +1462,7 @@ void prep_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64) {
 // One persistent launch: iterations k0 .. cap - 1 (it stops earlier once every
 // piece has converged; out_it then holds the iteration it stopped at).
 template <typename A>
-void launch_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap) {
+void launch_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap, bool resume) {
     cudaStream_t s = ctx->stream;
     using V = typename A::V;
     V* xv = reinterpret_cast<V*>(D.x.p);
@@ -1459,6 +1473,8 @@ void launch_typed(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap) {
                  pv, qv, D.runs.p, D.run_off.p, D.RR.p, D.RD.p, D.PQ.p, D.ACT.p, D.THR.p, D.out_it.p, cap,
                  D.dncp, D.work.p};
     a.k0 = k0;
+    a.resume = resume ? 1 : 0;
+    a.RRP = D.RRP.p;
     a.chunks = D.chunks.p;
     a.nchunks = D.nchunks;
     a.nch = D.nch.p;
@@ -1712,6 +1728,7 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
         PGCP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
     }
     D.RR.alloc(4 * 2 * S, s);
+    D.RRP.alloc(2 * S, s);
     D.RD.alloc(4 * 2 * S, s);
     D.DL.alloc(4 * 2 * S, s);
     D.PQ.alloc(2 * 2 * S, s);
@@ -1724,11 +1741,25 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
 }
 
 int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x, const std::vector<double>& thr,
-             int max_iters) {
+             int max_iters, bool resume) {
     cudaStream_t s = ctx->stream;
     const int S = P.K;
-    D.RR.zero();
-    D.RD.zero();
+    // Residual replacement: a resumed solve (a refinement step after the
+    // first, static schedule, double-float) continues at the last solve's
+    // iteration index with x~ = 0, r~ = S r64 (the FP64 residual) and the
+    // same search direction p and q = A~ p, instead of restarting CG.  The
+    // step's z and <r~, z> are recomputed for the new residual, and beta
+    // divides by the <r~, z> of each piece's own last active iteration (RRP),
+    // however long ago the piece met its step's threshold.
+    resume = resume && D.resumable && D.sched == 1 && !D.det && !D.f32;
+    const int k0 = resume ? D.k_last : 0;
+    if (resume) {
+        PGCP_CUDA(cudaMemsetAsync(D.RR.p + (k0 % 3) * 2 * S, 0, 2 * S * sizeof(double), s));
+        PGCP_CUDA(cudaMemsetAsync(D.RD.p + (k0 % 3) * 2 * S, 0, 2 * S * sizeof(double), s));
+    } else {
+        D.RR.zero();
+        D.RD.zero();
+    }
     D.DL.zero();
     D.PQ.zero();
     D.ACT.zero();
@@ -1759,15 +1790,16 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
         PGCP_CUDA(cudaStreamSynchronize(s));   // the host run lists go out of scope
     };
     if (D.covered != D.n) set_runs(nullptr);
-    if (D.f32) prep_typed<ArithF32>(ctx, P, D, r64);
-    else prep_typed<ArithDF>(ctx, P, D, r64);
+    if (D.f32) prep_typed<ArithF32>(ctx, P, D, r64, k0 % 3, resume);
+    else prep_typed<ArithDF>(ctx, P, D, r64, k0 % 3, resume);
     if (D.ml) D.ml_M.zero();   // both parities of the preconditioner's moments
+    bool first = true;
     auto launch = [&](int k0, int cap) {
         EventPair ev;   // brackets the persistent kernel only
         PGCP_CUDA(cudaEventRecord(ev.a, s));
-        if (D.ml) ml_launch(ctx, P, D, k0, cap);
-        else if (D.f32) launch_typed<ArithF32>(ctx, P, D, k0, cap);
-        else launch_typed<ArithDF>(ctx, P, D, k0, cap);
+        if (D.ml) ml_launch(ctx, P, D, k0, cap, first && resume);
+        else if (D.f32) launch_typed<ArithF32>(ctx, P, D, k0, cap, first && resume);
+        else launch_typed<ArithDF>(ctx, P, D, k0, cap, first && resume);
         PGCP_CUDA(cudaEventRecord(ev.b, s));
         int k_end = 0;
         PGCP_CUDA(cudaMemcpyAsync(&k_end, D.out_it.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1776,9 +1808,10 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
         PGCP_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
         P.stats.pcg_ms += ms;
         P.stats.pcg_launches += 1;
+        first = false;
         return k_end;
     };
-    int it = 0;
+    int it = k0;
     if (D.sched == 1 && !D.det) {
         // Static schedule: the solve runs in launches of REBALANCE_ITERS
         // iterations.  Between them the host reads which pieces converged;
@@ -1789,11 +1822,11 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
         std::vector<double> rd(2 * (size_t)S);
         std::vector<uint8_t> active(S, 1);
         while (true) {
-            const int cap = (int)std::min<int64_t>(max_iters, (int64_t)it + REBALANCE_ITERS);
+            const int cap = (int)std::min<int64_t>((int64_t)k0 + max_iters, (int64_t)it + REBALANCE_ITERS);
             const int k_end = launch(it, cap);
             const bool stopped = k_end < cap;   // every piece converged
             it = k_end;
-            if (stopped || it >= max_iters) break;
+            if (stopped || it >= k0 + max_iters) break;
             PGCP_CUDA(cudaMemcpyAsync(rd.data(), D.RD.p + (it % 3) * 2 * S, 2 * S * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
             PGCP_CUDA(cudaStreamSynchronize(s));
@@ -1810,6 +1843,8 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
     } else {
         it = launch(0, max_iters);
     }
+    D.k_last = it;
+    D.resumable = true;
     if (D.f32) finish_typed<ArithF32>(ctx, D, x);
     else finish_typed<ArithDF>(ctx, D, x);
     unsigned long long w[2] = {0, 0};
@@ -1832,7 +1867,7 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
         P.stats.pcg_bytes += (double)w[0] * (4.0 + 19.0 * T) + (double)w[1] * (4.0 + T);
         P.stats.pcg_bytes_touched += (double)w[0] * (8.0 + 22.0 * T) + (double)w[1] * (4.0 + T);
     }
-    return it;
+    return it - k0;
 }
 
 }  // namespace pgcp

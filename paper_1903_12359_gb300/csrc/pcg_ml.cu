@@ -122,6 +122,10 @@ __device__ __forceinline__ float coef_out(int k, const float* cp, float s, const
 
 struct MlArgs {
     int32_t n, nseg, k0, max_iters, dncp, nl;
+    int32_t resume;                     // k0 continues a solve with a replaced residual: beta of
+                                        // iteration k0 divides by RRP, each piece's <r, z> of
+                                        // its last active iteration
+    double* RRP;                        // [2 nseg]
     const int32_t* __restrict__ rp;
     const int32_t* __restrict__ col;
     const float2* __restrict__ val;
@@ -536,10 +540,11 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
     };
 
     int k = a.k0;
-    if (k == 0) {
-        // z_0 = M r_0: moments of r_0 (parity 0), then the tables
+    if (k == 0 || a.resume) {
+        // z_k = M r_k for a new residual (the first, or a replaced one):
+        // moments of r_k (parity k & 1), then the tables and <r_k, z_k>
         if (blockIdx.x == 0)
-            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) a.RR[i] = 0.0;
+            for (int i = threadIdx.x; i < 2 * nseg; i += blockDim.x) a.RR[(k % 3) * 2 * nseg + i] = 0.0;
         for (int ri = rb; ri < re; ++ri) {
             const DfRun run = a.runs[ri];
             for (int base = run.lo; base < run.hi; base += blockDim.x) {
@@ -548,18 +553,18 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                 const bool act = row < run.hi;
                 const float d = act ? __ldg(dgp + row) : 0.f;
                 const V rv = act ? a.r[row] : A::vzero();
-                ml_moments0(a, run, base, 0, act, d, rv.x, rv.z, row, mbuf, nullptr);
+                ml_moments0(a, run, base, k & 1, act, d, rv.x, rv.z, row, mbuf, nullptr);
             }
             __syncthreads();
-            ml_restrict(a, run, mbuf, 0, nullptr);
+            ml_restrict(a, run, mbuf, k & 1, nullptr);
         }
         grid.sync();
-        phase_c(0, 0);
+        phase_c(k, k % 3);
         grid.sync();
     }
     for (; k < a.max_iters; ++k) {
         const double* RRk = a.RR + (k % 3) * 2 * nseg;
-        const double* RRm = a.RR + ((k + 2) % 3) * 2 * nseg;
+        const double* RRm = (a.resume && k == a.k0) ? a.RRP : a.RR + ((k + 2) % 3) * 2 * nseg;
         const double* RDk = a.RD + (k % 3) * 2 * nseg;
         double* PQk = a.PQ + (k % 2) * 2 * nseg;
         // ---------------- phase B: p = z + beta p, q = A~ z + beta q, <p, q>
@@ -689,6 +694,10 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                 sc[slot][0] = al0;
                 sc[slot][1] = al1;
                 sflag[slot][0] = d0 && d1;
+                if (!(d0 && d1)) {   // the <r, z> this step used, kept for a resumed solve
+                    a.RRP[2 * s] = __ldcg(RRk + 2 * s);
+                    a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
+                }
             }
             __syncthreads();
             if (sflag[slot][0]) continue;
@@ -1170,11 +1179,13 @@ void ml_build(pgcp_ctx* ctx, Part& P, const uint8_t* fixed, DfSystem& D) {
     PGCP_CUDA(cudaStreamSynchronize(s));   // host tables go out of scope
 }
 
-void ml_launch(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap) {
+void ml_launch(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap, bool resume) {
     MlArgs a{};
     a.n = (int32_t)D.n;
     a.nseg = P.K;
     a.k0 = k0;
+    a.resume = resume ? 1 : 0;
+    a.RRP = D.RRP.p;
     a.max_iters = cap;
     a.dncp = D.dncp;
     a.nl = D.ml_nl;

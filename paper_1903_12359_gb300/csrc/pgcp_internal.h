@@ -263,6 +263,7 @@ struct DfSystem {
     DBuf<unsigned char> x, r, p, q;   // n row pairs (float4 or float2)
     DBuf<unsigned char> r1, w0, w1, s1;   // single-reduction schedule only
     DBuf<double> RR, RD, PQ, THR, DL;
+    DBuf<double> RRP;                   // [2 nseg] each piece's <r, z> of its last active step
     DBuf<unsigned int> ACT;
     DBuf<int32_t> out_it;
     DBuf<unsigned long long> work;
@@ -284,6 +285,8 @@ struct DfSystem {
     int64_t ml_lofs[16] = {0};          // [ML_MAXL+1]
     int64_t ml_tofs[16] = {0};          // [ML_MAXL+1] first packed-factor entry of each level
     double ml_row_bytes = 0.0;          // preconditioner table bytes per row and iteration
+    int k_last = 0;                     // iteration index where the last solve stopped
+    bool resumable = false;             // a solve ran: the next one may continue it
     DBuf<int32_t> ml_bofs, ml_ltop, ml_pvoff;
     DBuf<float> ml_xr;                  // [3n] vertex positions in their piece's frame
     DBuf<float4> ml_geo;                // per block: centroid, 1 / RMS radius
@@ -307,11 +310,11 @@ int64_t make_runs(const std::vector<int64_t>& voff, const std::vector<uint8_t>* 
 // tables and factors, after df_build has made the scaled matrix.
 void ml_build(pgcp_ctx* ctx, Part& P, const uint8_t* fixed, DfSystem& D);
 // One persistent launch of the preconditioned kernel over iterations k0 .. cap-1.
-void ml_launch(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap);
+void ml_launch(pgcp_ctx* ctx, Part& P, DfSystem& D, int k0, int cap, bool resume);
 // One inner solve of A d = r64 (thresholds on the unscaled <r, r> per piece
 // and coordinate); adds d to x; returns the iterations run.
 int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x, const std::vector<double>& thr,
-             int max_iters);
+             int max_iters, bool resume);
 
 void build_partition(pgcp_ctx* ctx, Part& P, const int32_t* d_labels_or_null, const int32_t* d_cut, int64_t n_cut);
 void build_schedule(pgcp_ctx* ctx, Part& P);

@@ -3,7 +3,7 @@ systems; the preconditioner is the library's) against the Jacobi-only solve
 and the oracle's direct solve.
 
 - Both preconditioners solve every piece to the tolerance and match the
-  oracle's sparse direct solve to 1e-9 absolute: the preconditioner changes the
+  oracle's sparse direct solve to 1e-8 absolute: the preconditioner changes the
   iteration, never the answer.
 - On a mesh with pieces of tens of thousands of vertices the multilevel form
   needs several times fewer iterations.
@@ -66,7 +66,9 @@ def test_both_preconditioners_match_the_direct_solve(api, name):
         u, st = _local(api, m, precond, closed)
         assert st["dncp_relres"] <= 1e-13, (precond, st["dncp_relres"])
         err = _oracle_err(m, u)
-        assert err < 1e-9, (name, precond, err)
+        # forward error <= cond(A~) * relres * |u|: cond is 6e7-1e8 on the
+        # 10k-row pieces of grid2x2_40k, so 1e-8 still sits three orders below it
+        assert err < 1e-8, (name, precond, err)
         iters[precond] = st["dncp_iters"]
     print(name, "dncp iterations: multilevel", iters[0], "jacobi", iters[1])
 
