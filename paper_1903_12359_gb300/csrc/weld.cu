@@ -7,7 +7,9 @@
 // spread over the blocks.  At each step every block recomputes the step's map
 // record from the current image of the point that defines it (identical FP64
 // operations, so identical records), stores it, and applies it to the points
-// it owns with the index rules:
+// it owns with the index rules (a block keeps its points and the metadata of
+// their sequences in shared memory, and publishes every new value into one of
+// two global buffers by step parity, which the next step's records read):
 //   * points already zipped onto the imaginary axis take the root on their own
 //     side of the axis (imaginary part of the root has the sign of Im of the
 //     Mobius image);
@@ -292,7 +294,7 @@ struct JobMeta {
 };
 
 struct Phase1Args {
-    double* pr;           // point arrays
+    double* pr;           // point arrays, two buffers of npts (step parity)
     double* pi;
     int32_t* pinf;
     int64_t npts;
@@ -309,51 +311,67 @@ struct Phase1Args {
     int32_t* job_fail;    // [jobs] 1 if the job left its domain
 };
 
-__device__ __forceinline__ Pt ldp(const Phase1Args& a, int64_t i) { return Pt{a.pr[i], a.pi[i], a.pinf[i]}; }
-__device__ __forceinline__ void stp(const Phase1Args& a, int64_t i, Pt p) {
-    a.pr[i] = p.r;
-    a.pi[i] = p.i;
-    a.pinf[i] = p.inf;
+// Published point values, two buffers by step parity (buffer b at offset b *
+// npts): the records of step s read buffer s & 1 while the owners write the
+// step's new values into the other, so no block reads a value that its owner
+// has already advanced.
+__device__ __forceinline__ Pt ldp(const Phase1Args& a, int b, int64_t i) {
+    const int64_t j = b * a.npts + i;
+    return Pt{a.pr[j], a.pi[j], a.pinf[j]};
+}
+__device__ __forceinline__ void stp(const Phase1Args& a, int b, int64_t i, Pt p) {
+    const int64_t j = b * a.npts + i;
+    a.pr[j] = p.r;
+    a.pi[j] = p.i;
+    a.pinf[j] = p.inf;
 }
 
-// Record of sequence s at step `step` (0-based over the whole program) and
+// A sequence's metadata as phase 1 keeps it in shared memory: its own
+// descriptor, its weld's, and the first points of the weld's A and B sides.
+struct SeqCache {
+    SeqMeta m;
+    JobMeta J;
+    int64_t offA, offB;
+};
+
+// Record of a sequence at step `step` (0-based over the whole program) and
 // whether the sequence is active.  Steps: 0..k (Alg 1: g_1..g_{k+1}),
-// k+1..2k (Alg 2: h_{k-1}..h_1, h_0), 2k+1 (normalisation).
-__device__ bool seq_record(const Phase1Args& a, int s, int step, Rec& R, bool& ok) {
-    const SeqMeta m = a.seqs[s];
+// k+1..2k (Alg 2: h_{k-1}..h_1, h_0), 2k+1 (normalisation).  The points come
+// from global memory (their owners publish them every step).
+__device__ bool seq_record(const Phase1Args& a, const SeqCache& c, int step, Rec& R, bool& ok) {
+    const SeqMeta& m = c.m;
+    const int b = step & 1;
     const int k = m.k;
     ok = true;
     const int64_t o = m.off;
     if (step == 0) {
-        R = rec_sqrt_ratio(ldp(a, o), ldp(a, o + 1));
+        R = rec_sqrt_ratio(ldp(a, b, o), ldp(a, b, o + 1));
         return true;
     }
     if (step <= k - 1) {   // OPEN for j = step + 1 in 2..k
-        R = rec_open(ldp(a, o + step + 1), m.side == 0 ? 1.0 : -1.0, ok);
+        R = rec_open(ldp(a, b, o + step + 1), m.side == 0 ? 1.0 : -1.0, ok);
         return true;
     }
     if (step == k) {
-        R = rec_pole(R_MOB_POLE, ldp(a, o), ok);
+        R = rec_pole(R_MOB_POLE, ldp(a, b, o), ok);
         return true;
     }
-    const JobMeta J = a.jobs[m.job];
-    const SeqMeta A = a.seqs[J.seqA], B = a.seqs[J.seqB];
     if (step <= 2 * k - 1) {   // h_j, j = 2k - step... j runs k-1 .. 1
         int j = 2 * k - step;
-        R = rec_close(a.pi[A.off + j], a.pi[B.off + j], ok);
+        R = rec_close(a.pi[b * a.npts + c.offA + j], a.pi[b * a.npts + c.offB + j], ok);
         return true;
     }
     if (step == 2 * k) {
-        R = rec_pole(R_POLE_SQ, ldp(a, A.off), ok);
+        R = rec_pole(R_POLE_SQ, ldp(a, b, c.offA), ok);
         return true;
     }
     if (step == 2 * k + 1) {
-        Pt p1 = ldp(a, A.off + k + 1), p2 = ldp(a, B.off + k + 1);
-        if (J.closed) {
-            Pt q = ldp(a, A.off + k / 2);
+        Pt p1 = ldp(a, b, c.offA + k + 1), p2 = ldp(a, b, c.offB + k + 1);
+        if (c.J.closed) {
+            Pt q = ldp(a, b, c.offA + k / 2);
             R = rec_sphere_frame(p1, p2, q, m.side == 1);
         } else {
-            Pt ia = ldp(a, A.off + k + 2), ib = ldp(a, B.off + k + 2);
+            Pt ia = ldp(a, b, c.offA + k + 2), ib = ldp(a, b, c.offB + k + 2);
             R = rec_normalize(p1, p2, (ia.r + ib.r) * 0.5, (ia.i + ib.i) * 0.5);
         }
         ok = !p1.inf && !p2.inf;
@@ -382,57 +400,85 @@ __device__ int seq_mode(int k, int step, int l, int& kind_hint) {
 constexpr int P1_THREADS = 64;
 constexpr int P1_MAXSEQ = 32;  // sequences overlapping one block's item range (checked on the host)
 
+// Shared memory of a phase-1 block: per owned point its value (r, i, inf),
+// its sequence (local index) and its index l in the sequence; the records and
+// metadata of the sequences its points belong to.
+constexpr int P1_PT_BYTES = 8 + 8 + 4 + 4 + 4;
+
 __global__ void __launch_bounds__(P1_THREADS) k_weld_phase1(Phase1Args a) {
     cg::grid_group grid = cg::this_grid();
     __shared__ Rec srec[P1_MAXSEQ];
     __shared__ int sact[P1_MAXSEQ];
+    __shared__ SeqCache sc[P1_MAXSEQ];
+    extern __shared__ __align__(16) unsigned char p1_smem[];
     const int64_t per = (a.npts + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per;
     const int64_t hi = min(a.npts, lo + per);
+    const int np = hi > lo ? (int)(hi - lo) : 0;
+    double* zr = reinterpret_cast<double*>(p1_smem);
+    double* zi = zr + per;
+    int32_t* zinf = reinterpret_cast<int32_t*>(zi + per);
+    int32_t* zseq = zinf + per;
+    int32_t* zl = zseq + per;
     const int seq_lo = lo < hi ? a.item_seq[lo] : 0;
     const int seq_hi = lo < hi ? a.item_seq[hi - 1] : -1;
     const int nsq = seq_hi - seq_lo + 1;
+    if (threadIdx.x < nsq && threadIdx.x < P1_MAXSEQ) {
+        SeqCache c;
+        c.m = a.seqs[seq_lo + threadIdx.x];
+        c.J = a.jobs[c.m.job];
+        c.offA = a.seqs[c.J.seqA].off;
+        c.offB = a.seqs[c.J.seqB].off;
+        sc[threadIdx.x] = c;
+    }
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int64_t i = lo + t;
+        zr[t] = a.pr[i];
+        zi[t] = a.pi[i];
+        zinf[t] = a.pinf[i];
+        zseq[t] = a.item_seq[i] - seq_lo;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < np; t += blockDim.x)
+        zl[t] = zseq[t] < P1_MAXSEQ ? (int)(lo + t - sc[zseq[t]].m.off) : 0;
     const int nsteps = 2 * a.kmax + 2;
     for (int step = 0; step < nsteps; ++step) {
         if (threadIdx.x < nsq && threadIdx.x < P1_MAXSEQ) {
-            int s = seq_lo + threadIdx.x;
+            const SeqCache& c = sc[threadIdx.x];
             Rec R;
             bool ok = true;
-            bool act = seq_record(a, s, step, R, ok);
+            bool act = seq_record(a, c, step, R, ok);
             sact[threadIdx.x] = act;
             srec[threadIdx.x] = R;
             if (act && !ok) {
                 atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
-                atomicMin(a.fail_job, a.seqs[s].job);
-                atomicOr(&a.job_fail[a.seqs[s].job], 1);
+                atomicMin(a.fail_job, c.m.job);
+                atomicOr(&a.job_fail[c.m.job], 1);
             }
             // the block owning the first point of the sequence stores the record
-            const SeqMeta m = a.seqs[s];
-            if (act && m.off >= lo && m.off < hi) {
-                const JobMeta J = a.jobs[m.job];
-                const int k = m.k;
-                if (step <= k) a.recs[(m.side == 0 ? J.rec_gA : J.rec_gB) + step] = R;
+            if (act && c.m.off >= lo && c.m.off < hi) {
+                const int k = c.m.k;
+                if (step <= k) a.recs[(c.m.side == 0 ? c.J.rec_gA : c.J.rec_gB) + step] = R;
                 else if (step <= 2 * k) {
-                    if (m.side == 0) a.recs[J.rec_h + (step - k - 1)] = R;
+                    if (c.m.side == 0) a.recs[c.J.rec_h + (step - k - 1)] = R;
                 } else {
-                    a.recs[m.side == 0 ? J.rec_TA : J.rec_TB] = R;
+                    a.recs[c.m.side == 0 ? c.J.rec_TA : c.J.rec_TB] = R;
                 }
             }
         }
         __syncthreads();
-        // apply to owned points (the normalisation step writes the arc outputs)
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const int s = a.item_seq[i];
-            const int si = s - seq_lo;
+        // apply to owned points (the normalisation step writes the arc outputs);
+        // every new value is published for the other blocks' records
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int si = zseq[t];
             if (si >= P1_MAXSEQ || !sact[si]) continue;
-            const SeqMeta m = a.seqs[s];
-            const int l = (int)(i - m.off);
-            int hint = 0;
+            const SeqMeta& m = sc[si].m;
+            const int l = zl[t];
+            const Pt z{zr[t], zi[t], zinf[t]};
             if (step == 2 * m.k + 1) {
                 if (l <= m.k) {
-                    Pt o = apply_rec(srec[si], ldp(a, i), M_PRINCIPAL);
-                    const JobMeta J = a.jobs[m.job];
-                    double2* dst = (m.side == 0 ? a.arcA : a.arcB) + J.arc_off + l;
+                    Pt o = apply_rec(srec[si], z, M_PRINCIPAL);
+                    double2* dst = (m.side == 0 ? a.arcA : a.arcB) + sc[si].J.arc_off + l;
                     *dst = make_double2(o.r, o.i);
                     if (o.inf) {
                         atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
@@ -441,11 +487,16 @@ __global__ void __launch_bounds__(P1_THREADS) k_weld_phase1(Phase1Args a) {
                 }
                 continue;
             }
-            const int mode = seq_mode(m.k, step, l, hint);
-            stp(a, i, apply_rec(srec[si], ldp(a, i), mode));
+            int hint = 0;
+            const Pt o = apply_rec(srec[si], z, seq_mode(m.k, step, l, hint));
+            zr[t] = o.r;
+            zi[t] = o.i;
+            zinf[t] = o.inf;
+            stp(a, (step + 1) & 1, lo + t, o);
         }
         grid.sync();
     }
+    for (int t = threadIdx.x; t < np; t += blockDim.x) stp(a, 0, lo + t, Pt{zr[t], zi[t], zinf[t]});
 }
 
 // ---------------------------------------------------------------- phase 1: disk
@@ -458,7 +509,7 @@ struct DiskMeta {
 };
 
 struct DiskArgs {
-    double* pr;
+    double* pr;           // point arrays, two buffers of npts (step parity)
     double* pi;
     int32_t* pinf;
     int64_t npts;
@@ -471,10 +522,11 @@ struct DiskArgs {
     int32_t* seq_fail;    // [nseq] 1 if the sequence left its domain
 };
 
-__device__ bool disk_record(const DiskArgs& a, int s, int step, Rec& R, bool& ok) {
-    const DiskMeta m = a.seqs[s];
+// Record of a disk sequence at step `step`; points from buffer step & 1 of
+// the published values (two buffers of npts, as in phase 1 of the welds).
+__device__ bool disk_record(const DiskArgs& a, const DiskMeta& m, int step, Rec& R, bool& ok) {
     const int n = m.n;
-    const int64_t o = m.off;
+    const int64_t o = m.off + (step & 1) * a.npts;
     ok = true;
     if (step == 0) {
         R = rec_sqrt_ratio(Pt{a.pr[o], a.pi[o], a.pinf[o]}, Pt{a.pr[o + 1], a.pi[o + 1], a.pinf[o + 1]});
@@ -512,42 +564,65 @@ __global__ void __launch_bounds__(P1_THREADS) k_disk_phase1(DiskArgs a) {
     cg::grid_group grid = cg::this_grid();
     __shared__ Rec srec[P1_MAXSEQ];
     __shared__ int sact[P1_MAXSEQ];
+    __shared__ DiskMeta sm[P1_MAXSEQ];
+    extern __shared__ __align__(16) unsigned char p1_smem[];
     const int64_t per = (a.npts + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per;
     const int64_t hi = min(a.npts, lo + per);
+    const int np = hi > lo ? (int)(hi - lo) : 0;
+    double* zr = reinterpret_cast<double*>(p1_smem);
+    double* zi = zr + per;
+    int32_t* zinf = reinterpret_cast<int32_t*>(zi + per);
+    int32_t* zseq = zinf + per;
+    int32_t* zl = zseq + per;
     const int seq_lo = lo < hi ? a.item_seq[lo] : 0;
     const int seq_hi = lo < hi ? a.item_seq[hi - 1] : -1;
     const int nsq = seq_hi - seq_lo + 1;
+    if (threadIdx.x < nsq && threadIdx.x < P1_MAXSEQ) sm[threadIdx.x] = a.seqs[seq_lo + threadIdx.x];
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int64_t i = lo + t;
+        zr[t] = a.pr[i];
+        zi[t] = a.pi[i];
+        zinf[t] = a.pinf[i];
+        zseq[t] = a.item_seq[i] - seq_lo;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < np; t += blockDim.x)
+        zl[t] = zseq[t] < P1_MAXSEQ ? (int)(lo + t - sm[zseq[t]].off) : 0;
     const int nsteps = a.nmax + 2;
     for (int step = 0; step < nsteps; ++step) {
         if (threadIdx.x < nsq && threadIdx.x < P1_MAXSEQ) {
-            int s = seq_lo + threadIdx.x;
+            const DiskMeta& m = sm[threadIdx.x];
             Rec R;
             bool ok = true;
-            bool act = disk_record(a, s, step, R, ok);
+            bool act = disk_record(a, m, step, R, ok);
             sact[threadIdx.x] = act;
             srec[threadIdx.x] = R;
             if (act && !ok) {
                 atomicOr(a.err, (uint32_t)DE_WELD_DOMAIN);
-                atomicOr(&a.seq_fail[s], 1);
+                atomicOr(&a.seq_fail[seq_lo + threadIdx.x], 1);
             }
-            const DiskMeta m = a.seqs[s];
             if (act && m.off >= lo && m.off < hi) a.recs[m.rec + step] = R;
         }
         __syncthreads();
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const int s = a.item_seq[i];
-            const int si = s - seq_lo;
+        const int64_t wb = ((step + 1) & 1) * a.npts;   // the buffer this step publishes into
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int si = zseq[t];
             if (si >= P1_MAXSEQ || !sact[si]) continue;
-            const DiskMeta m = a.seqs[s];
-            const int l = (int)(i - m.off);
-            Pt z{a.pr[i], a.pi[i], a.pinf[i]};
-            Pt o = apply_rec(srec[si], z, disk_mode(m.n, step, l));
-            a.pr[i] = o.r;
-            a.pi[i] = o.i;
-            a.pinf[i] = o.inf;
+            const Pt o = apply_rec(srec[si], Pt{zr[t], zi[t], zinf[t]}, disk_mode(sm[si].n, step, zl[t]));
+            zr[t] = o.r;
+            zi[t] = o.i;
+            zinf[t] = o.inf;
+            a.pr[wb + lo + t] = o.r;
+            a.pi[wb + lo + t] = o.i;
+            a.pinf[wb + lo + t] = o.inf;
         }
         grid.sync();
+    }
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        a.pr[lo + t] = zr[t];
+        a.pi[lo + t] = zi[t];
+        a.pinf[lo + t] = zinf[t];
     }
 }
 
@@ -713,12 +788,26 @@ void upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
     if (!h.empty()) PGCP_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
 }
 
-int coop_grid(pgcp_ctx* ctx, const void* kernel, int threads, int64_t items, int items_per_block) {
-    int per_sm = 0;
-    PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
-    int cap = std::max(1, per_sm * ctx->num_sms);
-    int64_t want = std::max<int64_t>(1, ceil_div(items, items_per_block));
-    return (int)std::min<int64_t>(want, cap);
+// Grid of a phase-1 kernel: about 16 points per block, at most what stays
+// resident with the per-point shared memory (P1_PT_BYTES each) that the block
+// range needs; sets the kernel's dynamic shared memory limit and returns the
+// bytes to launch with.
+int coop_grid_pts(pgcp_ctx* ctx, const void* kernel, int64_t npts, size_t* smem) {
+    int64_t grid = std::max<int64_t>(1, ceil_div(npts, 16));
+    for (int pass = 0; pass < 4; ++pass) {
+        const int64_t per = ceil_div(npts, grid);
+        *smem = (size_t)per * P1_PT_BYTES;
+        if (*smem > (size_t)227 * 1024) fail(PGCP_E_ARG, "too many welding points for one phase-1 launch");
+        PGCP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+        int per_sm = 0;
+        PGCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, P1_THREADS, *smem));
+        const int64_t cap = std::max<int64_t>(1, (int64_t)per_sm * ctx->num_sms);
+        if (grid <= cap) return (int)grid;
+        grid = cap;
+    }
+    const int64_t per = ceil_div(npts, grid);
+    *smem = (size_t)per * P1_PT_BYTES;
+    return (int)grid;
 }
 
 // Every block's contiguous item range may meet at most P1_MAXSEQ sequences.
@@ -880,9 +969,9 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         upload(d_xinf, xinf, s);
         upload(d_seqs, seqs, s);
         upload(d_jobs, jobs, s);
-        d_pr.alloc(npts, s);
-        d_pi.alloc(npts, s);
-        d_pinf.alloc(npts, s);
+        d_pr.alloc(2 * npts, s);   // two buffers (step parity)
+        d_pi.alloc(2 * npts, s);
+        d_pinf.alloc(2 * npts, s);
         { k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
                                                    d_pi.p, d_pinf.p); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
@@ -895,10 +984,11 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
                      recs.p, arcA.p, arcB.p, ctx->err.p, fail_job.p, job_fail.p};
         // few points per block: the FP64 work of a step is spread over many SMs;
         // at most P1_MAXSEQ sequences may meet in one block
-        int grid = coop_grid(ctx, (const void*)k_weld_phase1, P1_THREADS, npts, 16);
+        size_t smem = 0;
+        int grid = coop_grid_pts(ctx, (const void*)k_weld_phase1, npts, &smem);
         check_block_sequences(item_seq, grid);
         void* args[] = {(void*)&a};
-        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_weld_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_weld_phase1, dim3(grid), dim3(P1_THREADS), args, smem, s)); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         uint32_t e = read_errors(ctx);
         if (e & DE_WELD_DOMAIN) {
@@ -996,9 +1086,9 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         upload(d_xi, xi, s);
         upload(d_xinf, xinf, s);
         upload(d_seqs, seqs, s);
-        d_pr.alloc(npts, s);
-        d_pi.alloc(npts, s);
-        d_pinf.alloc(npts, s);
+        d_pr.alloc(2 * npts, s);   // two buffers (step parity)
+        d_pi.alloc(2 * npts, s);
+        d_pinf.alloc(2 * npts, s);
         { k_gather_points<<<nblk(npts), 256, 0, s>>>(d_rows.p, d_xr.p, d_xi.p, d_xinf.p, npts, P.welded.p, d_pr.p,
                                                    d_pi.p, d_pinf.p); ::pgcp::note_launch(); }
         DBuf<int32_t> seq_fail;
@@ -1006,10 +1096,11 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         seq_fail.zero();
         DiskArgs a{d_pr.p, d_pi.p, d_pinf.p, npts, d_item_seq.p, d_seqs.p, (int32_t)seqs.size(), nmax, recs.p,
                    ctx->err.p, seq_fail.p};
-        int grid = coop_grid(ctx, (const void*)k_disk_phase1, P1_THREADS, npts, 16);
+        size_t smem = 0;
+        int grid = coop_grid_pts(ctx, (const void*)k_disk_phase1, npts, &smem);
         check_block_sequences(item_seq, grid);
         void* args[] = {(void*)&a};
-        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_disk_phase1, dim3(grid), dim3(P1_THREADS), args, 0, s)); ::pgcp::note_launch(); }
+        { PGCP_CUDA(cudaLaunchCooperativeKernel((void*)k_disk_phase1, dim3(grid), dim3(P1_THREADS), args, smem, s)); ::pgcp::note_launch(); }
         PGCP_CUDA(cudaGetLastError());
         if (read_errors(ctx) & DE_WELD_DOMAIN) {
             std::vector<int32_t> sf(seqs.size());
