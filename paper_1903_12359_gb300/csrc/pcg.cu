@@ -626,7 +626,8 @@ SolveResult pcg_solve(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, do
         // CG with the residual replaced (df_solve).  The replacement must stay a
         // small change of the recurrence residual for the search direction to
         // remain usable, so a step stops long before the recurrence drifts away
-        // from the true residual (which happens near 2^-48 cond(A~)).
+        // from the true residual (which happens near 2^-48 cond(A~)).  FP32
+        // solves restart per step: continued FP32 CG took more iterations.
         constexpr double DF_STEP = 1e-3;
         const bool df_resume = !f32 && D.sched == 1 && !D.det;
         // Safeguard: near the double-float floor a continued step can break

@@ -861,13 +861,83 @@ __device__ __forceinline__ void ml_basis(const float* __restrict__ xr, float4 g,
 // inside the block, plus (weight to rows outside or fixed) m_i m_i^T), and
 // the area part G_K = sum_i m_i (m_next / 2 - m_prev / 2)^T over boundary rows
 // (PASS 2, full NF1 x NF1).  Symmetric parts are stored packed.
+// One row's contribution to a block's Gram (PASS 0), edge-form Laplacian
+// (PASS 1) or area (PASS 2) matrix; the block holds rows [r0, r1).
+template <int NF1, int PASS>
+__device__ __forceinline__ void gram_row(int i, int r0, int r1, const float* __restrict__ xr, float4 g,
+                                         const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                         const double* __restrict__ val, const double* __restrict__ diag,
+                                         const uint8_t* __restrict__ fixed, const int2* __restrict__ nbr,
+                                         double* acc) {
+    if (fixed[i]) return;
+    double mi[NF1];
+    ml_basis<NF1>(xr, g, i, mi);
+    if (PASS == 0) {
+        const double d = diag[i];
+        int t = 0;
+#pragma unroll
+        for (int p = 0; p < NF1; ++p)
+#pragma unroll
+            for (int q = p; q < NF1; ++q) acc[t++] += d * mi[p] * mi[q];
+    } else if (PASS == 1) {
+        double dl = 0.0;   // weight to neighbours outside the block or fixed
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int j = col[e];
+            if (j == i) continue;
+            const double w = -val[e];
+            if (j < r0 || j >= r1 || fixed[j]) {
+                dl += w;
+                continue;
+            }
+            if (j < i) continue;   // each inside edge once
+            double mj[NF1];
+            ml_basis<NF1>(xr, g, j, mj);
+            double dm[NF1];
+#pragma unroll
+            for (int p = 0; p < NF1; ++p) dm[p] = mi[p] - mj[p];
+            int t = 0;
+#pragma unroll
+            for (int p = 0; p < NF1; ++p)
+#pragma unroll
+                for (int q = p; q < NF1; ++q) acc[t++] += w * dm[p] * dm[q];
+        }
+        int t = 0;
+#pragma unroll
+        for (int p = 0; p < NF1; ++p)
+#pragma unroll
+            for (int q = p; q < NF1; ++q) acc[t++] += dl * mi[p] * mi[q];
+    } else {
+        const int2 pn = nbr[i];   // (prev, next) loop rows; -1 inside
+        if (pn.x < 0) return;
+        double v[NF1];
+#pragma unroll
+        for (int q = 0; q < NF1; ++q) v[q] = 0.0;
+        if (pn.y >= r0 && pn.y < r1 && !fixed[pn.y]) {
+            double mn[NF1];
+            ml_basis<NF1>(xr, g, pn.y, mn);
+#pragma unroll
+            for (int q = 0; q < NF1; ++q) v[q] += 0.5 * mn[q];
+        }
+        if (pn.x >= r0 && pn.x < r1 && !fixed[pn.x]) {
+            double mp[NF1];
+            ml_basis<NF1>(xr, g, pn.x, mp);
+#pragma unroll
+            for (int q = 0; q < NF1; ++q) v[q] -= 0.5 * mp[q];
+        }
+#pragma unroll
+        for (int p = 0; p < NF1; ++p)
+#pragma unroll
+            for (int q = 0; q < NF1; ++q) acc[p * NF1 + q] += mi[p] * v[q];
+    }
+}
+
 template <int NF1, int PASS>
 __global__ void __launch_bounds__(128) k_ml_gram(int l, int nb, int nseg, const int32_t* __restrict__ bofs_l,
                                                  const int32_t* __restrict__ pvoff, const float* __restrict__ xr,
                                                  const float4* __restrict__ geo, const int32_t* __restrict__ rp,
                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
                                                  const double* __restrict__ diag, const uint8_t* __restrict__ fixed,
-                                                 const int2* __restrict__ nbr, double* __restrict__ out) {
+                                                 const int2* __restrict__ nbr, double* __restrict__ out, int chunk) {
     constexpr int NS = NF1 * (NF1 + 1) / 2;
     constexpr int NO = PASS == 2 ? NF1 * NF1 : NS;
     const int b = blockIdx.x;
@@ -875,71 +945,14 @@ __global__ void __launch_bounds__(128) k_ml_gram(int l, int nb, int nseg, const 
     int s, r0, r1;
     ml_block_rows(bofs_l, nseg, l, pvoff, b, &s, &r0, &r1);
     const float4 g = geo[b];
+    // chunk blockIdx.y of the block's rows (chunk rows each); edges to rows of
+    // other chunks of the same block still count as inside (r0, r1 unchanged)
+    const int c0 = r0 + (int)blockIdx.y * chunk, c1 = min(r1, c0 + chunk);
     double acc[NO];
 #pragma unroll
     for (int i = 0; i < NO; ++i) acc[i] = 0.0;
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        if (fixed[i]) continue;
-        double mi[NF1];
-        ml_basis<NF1>(xr, g, i, mi);
-        if (PASS == 0) {
-            const double d = diag[i];
-            int t = 0;
-#pragma unroll
-            for (int p = 0; p < NF1; ++p)
-#pragma unroll
-                for (int q = p; q < NF1; ++q) acc[t++] += d * mi[p] * mi[q];
-        } else if (PASS == 1) {
-            double dl = 0.0;   // weight to neighbours outside the block or fixed
-            for (int e = rp[i]; e < rp[i + 1]; ++e) {
-                const int j = col[e];
-                if (j == i) continue;
-                const double w = -val[e];
-                if (j < r0 || j >= r1 || fixed[j]) {
-                    dl += w;
-                    continue;
-                }
-                if (j < i) continue;   // each inside edge once
-                double mj[NF1];
-                ml_basis<NF1>(xr, g, j, mj);
-                double dm[NF1];
-#pragma unroll
-                for (int p = 0; p < NF1; ++p) dm[p] = mi[p] - mj[p];
-                int t = 0;
-#pragma unroll
-                for (int p = 0; p < NF1; ++p)
-#pragma unroll
-                    for (int q = p; q < NF1; ++q) acc[t++] += w * dm[p] * dm[q];
-            }
-            int t = 0;
-#pragma unroll
-            for (int p = 0; p < NF1; ++p)
-#pragma unroll
-                for (int q = p; q < NF1; ++q) acc[t++] += dl * mi[p] * mi[q];
-        } else {
-            const int2 pn = nbr[i];   // (prev, next) loop rows; -1 inside
-            if (pn.x < 0) continue;
-            double v[NF1];
-#pragma unroll
-            for (int q = 0; q < NF1; ++q) v[q] = 0.0;
-            if (pn.y >= r0 && pn.y < r1 && !fixed[pn.y]) {
-                double mn[NF1];
-                ml_basis<NF1>(xr, g, pn.y, mn);
-#pragma unroll
-                for (int q = 0; q < NF1; ++q) v[q] += 0.5 * mn[q];
-            }
-            if (pn.x >= r0 && pn.x < r1 && !fixed[pn.x]) {
-                double mp[NF1];
-                ml_basis<NF1>(xr, g, pn.x, mp);
-#pragma unroll
-                for (int q = 0; q < NF1; ++q) v[q] -= 0.5 * mp[q];
-            }
-#pragma unroll
-            for (int p = 0; p < NF1; ++p)
-#pragma unroll
-                for (int q = 0; q < NF1; ++q) acc[p * NF1 + q] += mi[p] * v[q];
-        }
-    }
+    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+        gram_row<NF1, PASS>(i, r0, r1, xr, g, rp, col, val, diag, fixed, nbr, acc);
     // block reduction: warps by shuffles, then across the block's warps (1 to 4)
     __shared__ double sh[4][NO];
 #pragma unroll
@@ -954,9 +967,21 @@ __global__ void __launch_bounds__(128) k_ml_gram(int l, int nb, int nseg, const 
     for (int i = threadIdx.x; i < NO; i += blockDim.x) {
         double v = sh[0][i];
         for (int w = 1; w < nw; ++w) v += sh[w][i];
-        out[(int64_t)b * NO + i] = v;
+        out[((int64_t)b * gridDim.y + blockIdx.y) * NO + i] = v;
     }
 }
+
+// out[b][i] = sum over the block's chunks of part[b][c][i], in chunk order.
+__global__ void k_ml_chunk_sum(int64_t nbo, int no, int nchunk, const double* __restrict__ part,
+                               double* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nbo) return;
+    const int64_t b = t / no, i = t - b * no;
+    double v = 0.0;
+    for (int c = 0; c < nchunk; ++c) v += part[(b * nchunk + c) * no + i];
+    out[t] = v;
+}
+
 
 // Upper-triangular R (n x n, row-major full storage) with C ~ R^T R, dropping
 // every pivot at or below eps times its diagonal entry (that row of R stays 0).
@@ -1085,14 +1110,29 @@ void gram_level(cudaStream_t s, int l, int nb, int K, const DfSystem& D, const P
     GL.alloc((size_t)nb * NS, s);
     GK.alloc((size_t)nb * NF1 * NF1, s);
     const int32_t* bofs_l = D.ml_bofs.p + l * (K + 1);
-    // threads per block sized to the block's rows (16 * 4^l): 32 up to 64 rows, 64 for 256, else 128
+    // threads per CTA sized to the block's rows (16 * 4^l): 32 up to 64 rows,
+    // 64 for 256, else 128; blocks above 1024 rows are cut into 1024-row
+    // chunks, one CTA each, whose partial sums are added in chunk order
+    constexpr int CHUNK = 1024;
     const int nthr = l <= 1 ? 32 : (l == 2 ? 64 : 128);
-    { k_ml_gram<NF1, 0><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
-                                            P.val64.p, P.diag64.p, fixed, P.nb.p, Cs.p); ::pgcp::note_launch(); }
-    { k_ml_gram<NF1, 1><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
-                                            P.val64.p, P.diag64.p, fixed, P.nb.p, GL.p); ::pgcp::note_launch(); }
-    { k_ml_gram<NF1, 2><<<nb, nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
-                                            P.val64.p, P.diag64.p, fixed, P.nb.p, GK.p); ::pgcp::note_launch(); }
+    const int brows = 16 << (2 * l);
+    const int nchunk = brows > CHUNK ? brows / CHUNK : 1;
+    const int chunk = nchunk > 1 ? CHUNK : brows;
+    DBuf<double> part;
+    if (nchunk > 1) part.alloc((size_t)nb * nchunk * NF1 * NF1, s);
+    auto pass = [&](auto kern, int no, double* out) {
+        double* dst = nchunk > 1 ? part.p : out;
+        { kern<<<dim3(nb, nchunk), nthr, 0, s>>>(l, nb, K, bofs_l, D.ml_pvoff.p, D.ml_xr.p, geo, P.row_ptr.p, P.col.p,
+                                                 P.val64.p, P.diag64.p, fixed, P.nb.p, dst, chunk); ::pgcp::note_launch(); }
+        if (nchunk > 1) {
+            const int64_t nbo = (int64_t)nb * no;
+            { k_ml_chunk_sum<<<(unsigned)ceil_div(nbo, (int64_t)256), 256, 0, s>>>(nbo, no, nchunk, part.p, out);
+              ::pgcp::note_launch(); }
+        }
+    };
+    pass(k_ml_gram<NF1, 0>, NS, Cs.p);
+    pass(k_ml_gram<NF1, 1>, NS, GL.p);
+    pass(k_ml_gram<NF1, 2>, NF1 * NF1, GK.p);
     { k_ml_factor<NF1><<<nb, 32, 0, s>>>(nb, Cs.p, GL.p, GK.p, T, sep); ::pgcp::note_launch(); }
     PGCP_CUDA(cudaGetLastError());
 }

@@ -27,8 +27,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 #include "pgcp_internal.h"
@@ -893,6 +891,11 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
     DBuf<ChainRef> d_chains;
     upload(d_chains, chains, s);
     ctx->err.zero();
+    // position of a global vertex in the arc (or loop) being looked up, -1
+    // elsewhere: set for one weld's arc, read for its pieces' loops, reset
+    int32_t gmax = 0;
+    for (int32_t g : P.loop_glob) gmax = std::max(gmax, g);
+    std::vector<int64_t> gpos((size_t)gmax + 1, -1);
     // A mesh of a batch whose welding leaves its domain is dropped (status
     // NUMERIC, output NaN) and the others go on; a single mesh fails the call.
     std::vector<uint8_t> mfail(nmesh, 0);
@@ -1007,18 +1010,18 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             const WeldPlan& W = P.welds[wi];
             if (mfail[W.mesh]) continue;
             const JobMeta& J = all_jobs[wi];
-            std::unordered_map<int32_t, int> arcpos;
-            for (int l = 0; l <= W.k; ++l) arcpos[W.a_glob[l]] = l;
+            for (int l = 0; l <= W.k; ++l) gpos[W.a_glob[l]] = l;
             auto add_piece = [&](int32_t pc, int side) {
                 for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) {
                     p2_rows.push_back((int32_t)P.loop_rows[t]);
-                    auto it = arcpos.find(P.loop_glob[t]);
-                    p2_arc.push_back(it == arcpos.end() ? -1 : (int32_t)(J.arc_off + it->second));
+                    const int64_t l = gpos[P.loop_glob[t]];
+                    p2_arc.push_back(l < 0 ? -1 : (int32_t)(J.arc_off + l));
                     p2_chain.push_back(2 * wi + side);
                 }
             };
             for (int32_t pc : W.members) add_piece(pc, 0);
             for (int32_t pc : W.b_members) add_piece(pc, 1);
+            for (int l = 0; l <= W.k; ++l) gpos[W.a_glob[l]] = -1;
         }
         DBuf<int32_t> d2_rows, d2_arc, d2_chain;
         upload(d2_rows, p2_rows, s);
@@ -1061,18 +1064,21 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             const MeshInfo& M = P.meshes[mi];
             const auto& loop = disk_loop[mi];
             // rows: copy in the lowest-label piece of the mesh holding the vertex
-            std::unordered_map<int32_t, int64_t> grow;
             for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece; ++pc)
-                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) grow.emplace(P.loop_glob[t], P.loop_rows[t]);
+                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t)
+                    if (gpos[P.loop_glob[t]] < 0) gpos[P.loop_glob[t]] = P.loop_rows[t];
             DiskMeta m{(int64_t)item_seq.size(), (int32_t)loop.size() - 1, 0, disk_rec[mi]};
             nmax = std::max(nmax, m.n);
             const int sid = (int)seqs.size();
             seqs.push_back(m);
             for (int32_t g : loop) {
+                if (gpos[g] < 0) fail(PGCP_E_ARG, "disk loop vertex on no piece loop of its mesh");
                 item_seq.push_back(sid);
-                rows.push_back((int32_t)grow.at(g));
+                rows.push_back((int32_t)gpos[g]);
                 xr.push_back(0); xi.push_back(0); xinf.push_back(0);
             }
+            for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece; ++pc)
+                for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) gpos[P.loop_glob[t]] = -1;
             double cref = by_mesh[mi].empty() ? 0.0 : -1.0;
             item_seq.push_back(sid); rows.push_back(-1); xr.push_back(cref); xi.push_back(0); xinf.push_back(0);
         }
@@ -1115,15 +1121,15 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         for (int mi = 0; mi < nmesh; ++mi) {
             if (mfail[mi]) continue;
             const MeshInfo& M = P.meshes[mi];
-            std::unordered_map<int32_t, int> bpos;
-            for (size_t l = 0; l < disk_loop[mi].size(); ++l) bpos[disk_loop[mi][l]] = (int)l;
+            for (size_t l = 0; l < disk_loop[mi].size(); ++l) gpos[disk_loop[mi][l]] = (int64_t)l;
             for (int32_t pc = M.piece0; pc < M.piece0 + M.npiece; ++pc)
                 for (int64_t t = P.loff[pc]; t < P.loff[pc + 1]; ++t) {
                     p2_rows.push_back((int32_t)P.loop_rows[t]);
-                    auto it = bpos.find(P.loop_glob[t]);
-                    p2_arc.push_back(it == bpos.end() ? -1 : (int32_t)(seqs[mi].off + it->second));
+                    const int64_t l = gpos[P.loop_glob[t]];
+                    p2_arc.push_back(l < 0 ? -1 : (int32_t)(seqs[mi].off + l));
                     p2_chain.push_back(disk_chain[mi]);
                 }
+            for (int32_t g : disk_loop[mi]) gpos[g] = -1;
         }
         // sequence images as double2
         DBuf<double2> img;
