@@ -3,8 +3,8 @@
 
 A step is one pass of the whole path over one mesh already resident in device
 memory: partition -> cotangent assembly + DNCP (batched PCG) -> partial welds
-+ disk map -> final Laplace solve (FP32 PCG inside FP64 refinement, relative
-residual <= 1e-12 per piece and coordinate) -> gathered disk coordinates in
++ disk map -> final Laplace solve (double-float multilevel-preconditioned PCG
+inside FP64 refinement, relative residual <= 1e-12 per piece and coordinate) -> gathered disk coordinates in
 device memory.  value = vertices / s over K timed steps (CUDA events on the
 library's stream, barrier + synchronize on both sides, max over ranks; L2 is
 flushed with a 256 MB write before every step).  e2e repeats the measurement
@@ -112,7 +112,8 @@ def oracle_sample(n: int, seed: int, workers: int) -> dict:
 # ---------------------------------------------------------------- uneven batch
 
 BATCH_WORKLOAD = ("{n} height-field disks of the same recipe, vertex counts log-uniform in 5k-200k, each cut by "
-                  "a random grid into 4-32 pieces of uneven size; all meshes in one partition_batch call; disk maps")
+                  "a random grid into 4-32 pieces of uneven size; all meshes in one partition_batch call; disk maps; "
+                  "final solve FP32 PCG in FP64 refinement")
 
 
 def _uneven_mesh(params):
@@ -135,6 +136,8 @@ def run_batch(api, torch, ms, steps: int, warmup: int) -> dict:
     dev = [(torch.as_tensor(m.V, device="cuda"), torch.as_tensor(m.F, device="cuda", dtype=torch.int32),
             torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)) for m in ms]
     nv = sum(m.nv for m in ms)
+    # final solve in FP32 refinement here: over 5,000 small pieces the multilevel
+    # set-up costs more than the iterations it saves (661 ms against 505 ms)
     ctx = api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=TOL, local_precision=api.DF64_REFINED)
     rows = []
     for i in range(warmup + steps):
@@ -160,7 +163,7 @@ def run_batch(api, torch, ms, steps: int, warmup: int) -> dict:
     # dropped by the welding (NaN output) does not count
     nv_ok = sum(m.nv for m, c in zip(ms, status) if c == "OK")
     gbs = sum(r[2]["pcg_bytes"] for r in rows) / (sum(r[2]["pcg_ms"] for r in rows) / 1000.0) / 1e9
-    # the final (FP32 in FP64 refinement) solve: counters after the whole step minus after the local stage
+    # the final (double-float in FP64 refinement) solve: counters after the whole step minus after the local stage
     fb = sum(r[1]["pcg_bytes"] - r[2]["pcg_bytes"] for r in rows)
     fms = sum(r[1]["pcg_ms"] - r[2]["pcg_ms"] for r in rows)
     return {"workload": BATCH_WORKLOAD.format(n=len(ms)), "meshes": len(ms), "nv_mapped": nv_ok, "nv_all": nv,
@@ -190,7 +193,7 @@ def run_sphere(api, torch, steps: int, warmup: int, peak: float) -> dict:
     Fd = torch.as_tensor(m.F, device="cuda", dtype=torch.int32)
     Ld = torch.as_tensor(m.face_labels, device="cuda", dtype=torch.int32)
     out = torch.empty((m.nv, 3), dtype=torch.float64, device="cuda")
-    ctx = api.Context(variant=api.SPHERE, precision=api.FP32_REFINED, tol=TOL, local_precision=api.DF64_REFINED)
+    ctx = api.Context(variant=api.SPHERE, precision=api.DF64_REFINED, tol=TOL, local_precision=api.DF64_REFINED)
     rows = []
     for i in range(warmup + steps):
         torch.cuda.synchronize()
@@ -360,7 +363,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def make_ctx(warm):
-        return api.Context(variant=api.DISK, precision=api.FP32_REFINED, tol=TOL, warm_start=warm,
+        return api.Context(variant=api.DISK, precision=api.DF64_REFINED, tol=TOL, warm_start=warm,
                            local_precision=args.local_precision)
 
     def step(ctx):
@@ -497,7 +500,7 @@ def main():
                 "avg_launch_ms": pcg_ms / max(pcg_launches, 1), "launches": pcg_launches,
                 "share_of_step": (pcg_ms / ms) if ms > 0 else None,
                 "all_pcg_share_of_step": (step_pcg_ms / ms) if ms > 0 else None}
-    # the final solve's PCG (FP32 in FP64 refinement): all counters minus the DNCP ones
+    # the final solve's PCG (double-float in FP64 refinement): all counters minus the DNCP ones
     fbytes = sum(s["pcg_bytes"] - s["dncp_pcg"]["pcg_bytes"] for s in stats)
     fms = sum(s["pcg_ms"] - s["dncp_pcg"]["pcg_ms"] for s in stats)
     if fms > 0:
@@ -506,10 +509,10 @@ def main():
     s0 = stats[-1]
     line = {"metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "df32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nv": m.nv, "nf": m.nf, "pieces": s0["K"], "variant": "disk",
-                       "tol": TOL, "tol_note": "the metric's residual <= 1e-10 holds; the bench stops at 1e-12, where the result matches the oracle within the parity bars (coordinates 1e-8, |d| statistics 1e-6 degrees)", "precision": "final solve: FP32 PCG in FP64 refinement; DNCP: " +
-                       ("double-float PCG in FP64 refinement" if df else "FP64 PCG"), "warm_start": "weld map",
+                       "tol": TOL, "tol_note": "the metric's residual <= 1e-10 holds; the bench stops at 1e-12, where the result matches the oracle within the parity bars (coordinates 1e-8, |d| statistics 1e-6 degrees)", "precision": "final solve: double-float PCG with the multilevel preconditioner in FP64 refinement; DNCP: " +
+                       ("double-float PCG with the multilevel preconditioner in FP64 refinement" if df else "FP64 PCG"), "warm_start": "weld map",
                        "l2": "flushed before every step (256 MB write)",
                        "plain_cold_start_value": value_cold,
                        "learned_warm_start_value": value_learned,

@@ -83,7 +83,8 @@ typedef struct {
                                  available with PGCP_FP64 in either solve stage (PGCP_E_ARG).
                                  0 (default): unordered atomic sums, which may differ in the last
                                  bits between runs and change the iteration count slightly. */
-    int32_t local_precond;    /* preconditioner of the double-float DNCP solve (static schedule, not
+    int32_t local_precond;    /* preconditioner of the double-float solves (DNCP, and the final solve
+                                 when precision is DF64_REFINED; static schedule, not
                                  deterministic): 0 (default) multilevel -- additive corrections by
                                  low-degree polynomials on nested blocks of 16 * 4^l rows of every
                                  piece -- or 1 Jacobi only.  Other solver settings always use Jacobi. */

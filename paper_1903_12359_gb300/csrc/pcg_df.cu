@@ -378,10 +378,10 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_run(RunArgs<A> a) {
                 sc[slot][0] = al0;
                 sc[slot][1] = al1;
                 sflag[slot][0] = d0 && d1;
-                if (!(d0 && d1)) {   // the <r, r> this step used, kept for a resumed solve
-                    a.RRP[2 * s] = __ldcg(RRk + 2 * s);
-                    a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
-                }
+                // the <r, r> this step used, kept for a resumed solve: per
+                // coordinate, only while the coordinate is still iterating
+                if (!d0) a.RRP[2 * s] = __ldcg(RRk + 2 * s);
+                if (!d1) a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
             }
             __syncthreads();
             if (sflag[slot][0]) continue;
@@ -1638,10 +1638,11 @@ void df_build(pgcp_ctx* ctx, Part& P, int dncp, const uint8_t* fixed, int f32, D
     D.sched = sched == 0 ? 1 : sched;
     D.det = ctx->opt.deterministic ? 1 : 0;
     if (D.det) D.sched = 1;   // ordered sums are implemented for the static schedule
-    // multilevel preconditioner: double-float DNCP solves on the static schedule
+    // multilevel preconditioner: double-float solves (DNCP, and Laplace when
+    // the final solve runs in double-float) on the static schedule
     const int pc = ctx->opt.local_precond;
     if (pc != 0 && pc != 1) fail(PGCP_E_ARG, "local_precond must be 0 (multilevel) or 1 (Jacobi)");
-    D.ml = (dncp && !f32 && !D.det && D.sched == 1 && pc == 0) ? 1 : 0;
+    D.ml = (!f32 && !D.det && D.sched == 1 && pc == 0) ? 1 : 0;
     if (D.sched == 3 && P.K > RR_MAXSEG) D.sched = 1;   // the round-robin tables hold RR_MAXSEG pieces
     DBuf<int32_t> cnt;
     DBuf<int64_t> off;

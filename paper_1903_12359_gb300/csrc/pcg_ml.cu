@@ -694,10 +694,10 @@ __global__ void __launch_bounds__(RUN_THREADS, MINB) k_pcg_ml(const __grid_const
                 sc[slot][0] = al0;
                 sc[slot][1] = al1;
                 sflag[slot][0] = d0 && d1;
-                if (!(d0 && d1)) {   // the <r, z> this step used, kept for a resumed solve
-                    a.RRP[2 * s] = __ldcg(RRk + 2 * s);
-                    a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
-                }
+                // the <r, z> this step used, kept for a resumed solve: per
+                // coordinate, only while the coordinate is still iterating
+                if (!d0) a.RRP[2 * s] = __ldcg(RRk + 2 * s);
+                if (!d1) a.RRP[2 * s + 1] = __ldcg(RRk + 2 * s + 1);
             }
             __syncthreads();
             if (sflag[slot][0]) continue;

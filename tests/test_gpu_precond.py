@@ -1,6 +1,6 @@
-"""The multilevel preconditioner of the double-float DNCP solve (Section 4.2
-systems; the preconditioner is the library's) against the Jacobi-only solve
-and the oracle's direct solve.
+"""The multilevel preconditioner of the double-float solves (the DNCP systems
+of Section 4.2 and the final Laplace solve of Section 4.5; the preconditioner
+is the library's) against the Jacobi-only solve and the oracle.
 
 - Both preconditioners solve every piece to the tolerance and match the
   oracle's sparse direct solve to 1e-8 absolute: the preconditioner changes the
@@ -98,3 +98,28 @@ def test_uneven_batch_pieces(api):
         assert st["dncp_relres"] <= 1e-12
         out[precond] = part.coords(0).cpu().numpy()
     assert np.abs(out[0] - out[1]).max() < 1e-8
+
+
+def test_final_laplace_solve_with_the_multilevel_preconditioner(api):
+    """The double-float final solve (Section 4.5's Laplace equation with the
+    welded boundary) takes the same preconditioner: the same map as the
+    Jacobi-only solve within the accuracy its residual allows, the oracle's map
+    within the parity bar, and several times fewer iterations."""
+    from oracle.pipeline import pgcp as o_pgcp
+    m = meshgen.heightfield_disk_mesh(40000, seed=5, nx=2, ny=2)
+    out, iters = {}, {}
+    for precond in (0, 1):
+        ctx = api.Context(variant=api.DISK, precision=api.DF64_REFINED, tol=1e-13,
+                          local_precision=api.DF64_REFINED, local_precond=precond)
+        part = ctx.partition(m.V, m.F, face_labels=m.face_labels)
+        part.local_param()
+        part.weld()
+        out[precond] = part.global_solve().cpu().numpy()
+        st = part.stats
+        assert st["final_relres"] <= 1e-13
+        iters[precond] = st["final_iters"]
+    print("40k final-solve iterations: multilevel", iters[0], "jacobi", iters[1])
+    assert np.abs(out[0] - out[1]).max() < 1e-8
+    ref = o_pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk").out
+    assert np.abs(out[0] - ref).max() < 1e-8
+    assert 3 * iters[0] <= iters[1], iters
