@@ -1820,7 +1820,16 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
         // cover, the runs are rebuilt over those rows alone, so the remaining
         // pieces spread over every block again.  The per-piece accumulators
         // and vectors carry over, and the iteration index continues.
-        std::vector<double> rd(2 * (size_t)S);
+        //
+        // With the multilevel preconditioner a step also ends when it stalls:
+        // every unconverged piece (coordinate, for Laplace) has gone
+        // STALL_ITERS iterations without halving its residual norm squared.
+        // That happens only at the double-float floor, where the step cannot
+        // reach its threshold; the refinement loop then takes over (normal
+        // progress halves it about every hundred iterations).
+        constexpr int STALL_ITERS = 2048;
+        std::vector<double> rd(2 * (size_t)S), ref(2 * (size_t)S, INFINITY);
+        std::vector<int> mark(2 * (size_t)S, it);
         std::vector<uint8_t> active(S, 1);
         while (true) {
             const int cap = (int)std::min<int64_t>((int64_t)k0 + max_iters, (int64_t)it + REBALANCE_ITERS);
@@ -1832,13 +1841,29 @@ int df_solve(pgcp_ctx* ctx, Part& P, DfSystem& D, const double2* r64, double2* x
                                       cudaMemcpyDeviceToHost, s));
             PGCP_CUDA(cudaStreamSynchronize(s));
             int64_t rows = 0;
+            bool progress = false;
+            auto watch = [&](int e, double v) {
+                if (v <= 0.5 * ref[e]) {
+                    ref[e] = v;
+                    mark[e] = it;
+                }
+                if (it - mark[e] < STALL_ITERS) progress = true;
+            };
             for (int i = 0; i < S; ++i) {
                 bool done;
-                if (D.dncp) done = rd[2 * i] + rd[2 * i + 1] <= thr[2 * i] + thr[2 * i + 1];
-                else done = rd[2 * i] <= thr[2 * i] && rd[2 * i + 1] <= thr[2 * i + 1];
+                if (D.dncp) {
+                    done = rd[2 * i] + rd[2 * i + 1] <= thr[2 * i] + thr[2 * i + 1];
+                    if (!done) watch(2 * i, rd[2 * i] + rd[2 * i + 1]);
+                } else {
+                    const bool d0 = rd[2 * i] <= thr[2 * i], d1 = rd[2 * i + 1] <= thr[2 * i + 1];
+                    done = d0 && d1;
+                    if (!d0) watch(2 * i, rd[2 * i]);
+                    if (!d1) watch(2 * i + 1, rd[2 * i + 1]);
+                }
                 active[i] = done ? 0 : 1;
                 if (!done) rows += P.voff[i + 1] - P.voff[i];
             }
+            if (D.ml && rows > 0 && !progress) break;
             if (rows > 0 && 4 * rows < 3 * D.covered) set_runs(&active);
         }
     } else {
