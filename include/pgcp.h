@@ -58,7 +58,9 @@ typedef struct {
     int32_t max_iters;        /* PCG iterations per solve (inner solves for FP32_REFINED) */
     int32_t max_refine;       /* outer FP64 refinement steps (FP32_REFINED) */
     double  inner_tol;        /* relative residual reduction of one inner FP32 solve */
-    int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve */
+    int32_t warm_start;       /* pgcp_warm_start for the final Laplace solve; with PGCP_WARM_COLD the weld
+                                 skips the interior map, and interior welded coordinates keep their
+                                 local (DNCP) values */
     int32_t interior_map_fp64;/* 1: weld-map the interior in FP64 (else FP32) */
     int32_t block_rows_log2;  /* PCG rows per block tile (autotuner output; 0 = default) */
     int32_t local_precision;  /* pgcp_precision of the DNCP solve: default DF64_REFINED (FP32_REFINED

@@ -1155,8 +1155,10 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         }
         check_finite("a disk-mapped boundary point is not finite");
     }
-    // ---- interior weld map: every chain of each piece, in order
-    {
+    // ---- interior weld map: every chain of each piece, in order (the warm
+    // start of the final solve, and the learned start's input; a cold start
+    // uses neither, so the interiors then keep their local coordinates)
+    if (o.warm_start != PGCP_WARM_COLD) {
         std::vector<std::vector<int32_t>> pch(P.K);
         for (size_t w = 0; w < P.welds.size(); ++w) {
             const WeldPlan& W = P.welds[w];

@@ -123,3 +123,19 @@ def test_final_laplace_solve_with_the_multilevel_preconditioner(api):
     ref = o_pgcp(m.V, m.F, face_labels=m.face_labels, variant="disk").out
     assert np.abs(out[0] - ref).max() < 1e-8
     assert 3 * iters[0] <= iters[1], iters
+
+
+def test_unreachable_tolerance_fails_after_bounded_work(api):
+    """A tolerance below the double-float floor ends in NO_CONVERGENCE after the
+    refinement steps, each cut short once it stalls (2,048 iterations without
+    halving the residual norm squared), not after max_iters per step."""
+    m = meshgen.heightfield_disk_mesh(150000, seed=1, nx=2, ny=2)
+    ctx = api.Context(variant=1, precision=0, tol=1e-16, local_precision=api.DF64_REFINED)
+    part = ctx.partition(m.V, m.F, face_labels=m.face_labels)
+    with pytest.raises(api.PgcpError) as e:
+        part.local_param()
+    assert e.value.code == "NO_CONVERGENCE"
+    st = part.get_stats()
+    print("tol 1e-16: dncp iterations", st["dncp_iters"], "relres", st["dncp_relres"])
+    assert st["dncp_iters"] < 40000, st["dncp_iters"]
+    assert st["dncp_relres"] < 1e-11
