@@ -633,18 +633,20 @@ struct ChainRef {         // a chain = consecutive record ranges
 };
 
 // FP64: apply one chain to listed rows (principal root); rows listed with
-// arc >= 0 take arc value instead.
+// arc >= 0 take arc value instead, from arc_b for odd chains (the B sides of
+// welds) when arc_b is given, else from arc_vals.  Every item writes only its
+// own row, so both sides of every weld of a round run in one launch.
 __global__ void k_phase2_boundary(const int32_t* __restrict__ rows, const int32_t* __restrict__ arc_idx,
                                   const int32_t* __restrict__ item_chain, int64_t nitems,
                                   const ChainRef* __restrict__ chains, const Rec* __restrict__ recs,
-                                  const double2* __restrict__ arc_vals, double2* __restrict__ W,
-                                  uint32_t* err) {
+                                  const double2* __restrict__ arc_vals, const double2* __restrict__ arc_b,
+                                  double2* __restrict__ W, uint32_t* err) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nitems) return;
     const int row = rows[t];
     const int ai = arc_idx[t];
     if (ai >= 0) {
-        W[row] = arc_vals[ai];
+        W[row] = (arc_b && (item_chain[t] & 1)) ? arc_b[ai] : arc_vals[ai];
         return;
     }
     const ChainRef c = chains[item_chain[t]];
@@ -1027,30 +1029,15 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
         upload(d2_rows, p2_rows, s);
         upload(d2_arc, p2_arc, s);
         upload(d2_chain, p2_chain, s);
-        // A-side copies first (arc values of side A), then side B
+        // both sides of every weld of the round in one launch (32-thread
+        // blocks: few points per round, spread over every SM)
         const int64_t n2 = (int64_t)p2_rows.size();
-        // two launches so each side reads its own arc values
-        std::vector<int32_t> sideB(n2);
-        {
-            std::vector<int32_t> ra, aa, ca, rb, ab, cbv;
-            for (int64_t t = 0; t < n2; ++t) {
-                if (p2_chain[t] % 2 == 0) { ra.push_back(p2_rows[t]); aa.push_back(p2_arc[t]); ca.push_back(p2_chain[t]); }
-                else { rb.push_back(p2_rows[t]); ab.push_back(p2_arc[t]); cbv.push_back(p2_chain[t]); }
-            }
-            DBuf<int32_t> dra, daa, dca, drb, dab, dcb;
-            upload(dra, ra, s); upload(daa, aa, s); upload(dca, ca, s);
-            upload(drb, rb, s); upload(dab, ab, s); upload(dcb, cbv, s);
-            if (!ra.empty())
-                { k_phase2_boundary<<<nblk(ra.size(), 64), 64, 0, s>>>(dra.p, daa.p, dca.p, (int64_t)ra.size(),
-                                                                     d_chains.p, recs.p, arcA.p, P.welded.p,
-                                                                     ctx->err.p); ::pgcp::note_launch(); }
-            if (!rb.empty())
-                { k_phase2_boundary<<<nblk(rb.size(), 64), 64, 0, s>>>(drb.p, dab.p, dcb.p, (int64_t)rb.size(),
-                                                                     d_chains.p, recs.p, arcB.p, P.welded.p,
-                                                                     ctx->err.p); ::pgcp::note_launch(); }
+        if (n2 > 0) {
+            { k_phase2_boundary<<<nblk(n2, 32), 32, 0, s>>>(d2_rows.p, d2_arc.p, d2_chain.p, n2, d_chains.p, recs.p,
+                                                          arcA.p, arcB.p, P.welded.p, ctx->err.p); ::pgcp::note_launch(); }
             PGCP_CUDA(cudaGetLastError());
-            PGCP_CUDA(cudaStreamSynchronize(s));
         }
+        PGCP_CUDA(cudaStreamSynchronize(s));
     }
     check_finite("a welded boundary point is not finite");
     // ---- disk constraint
@@ -1147,8 +1134,8 @@ void run_welds(pgcp_ctx* ctx, Part& P) {
             upload(d2_arc, p2_arc, s);
             upload(d2_chain, p2_chain, s);
             if (!p2_rows.empty())
-                { k_phase2_boundary<<<nblk(p2_rows.size(), 64), 64, 0, s>>>(
-                    d2_rows.p, d2_arc.p, d2_chain.p, (int64_t)p2_rows.size(), d_chains.p, recs.p, img.p,
+                { k_phase2_boundary<<<nblk(p2_rows.size(), 32), 32, 0, s>>>(
+                    d2_rows.p, d2_arc.p, d2_chain.p, (int64_t)p2_rows.size(), d_chains.p, recs.p, img.p, nullptr,
                     P.welded.p, ctx->err.p); ::pgcp::note_launch(); }
             PGCP_CUDA(cudaGetLastError());
             PGCP_CUDA(cudaStreamSynchronize(s));
