@@ -788,12 +788,12 @@ void upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
     if (!h.empty()) PGCP_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
 }
 
-// Grid of a phase-1 kernel: about 16 points per block, at most what stays
+// Grid of a phase-1 kernel: one point per thread, at most what stays
 // resident with the per-point shared memory (P1_PT_BYTES each) that the block
 // range needs; sets the kernel's dynamic shared memory limit and returns the
 // bytes to launch with.
 int coop_grid_pts(pgcp_ctx* ctx, const void* kernel, int64_t npts, size_t* smem) {
-    int64_t grid = std::max<int64_t>(1, ceil_div(npts, 16));
+    int64_t grid = std::max<int64_t>(1, ceil_div(npts, (int64_t)P1_THREADS));
     for (int pass = 0; pass < 4; ++pass) {
         const int64_t per = ceil_div(npts, grid);
         *smem = (size_t)per * P1_PT_BYTES;
