@@ -60,7 +60,8 @@ def bench_case():
 @pytest.mark.parametrize("tol", [1e-10, 1e-12])
 def test_bench_mesh_matches_oracle(api, bench_case, tol):
     m, ref, ad = bench_case
-    ctx = api.Context(variant=api.DISK, precision=api.DF64_REFINED, tol=tol, local_precision=api.DF64_REFINED)
+    ctx = api.Context(variant=api.DISK, precision=api.DF64_REFINED, tol=tol, local_precision=api.DF64_REFINED,
+                      warm_start=api.WARM_COLD)
     part = ctx.partition(m.V, m.F, face_labels=m.face_labels)
     part.local_param()
     local = part.coords(0).cpu().numpy()
